@@ -1,0 +1,302 @@
+/*
+ * xm.h -- C ABI of the B300 directed subgraph matcher.
+ *
+ * Method: XMiner, "Efficient Directed Subgraph Matching with Pattern
+ * Reduction" (Yuan, Wang, Ma, He, Liu; arXiv 2404.11105).
+ *
+ * Problem (Sec. 2, Defs. 2.1-2.2 and the vertex/edge constraints after
+ * them): a data digraph G = (V, E) and a weakly connected pattern digraph
+ * P = (V_P, E_P) given by its arc list (Sec. 5.4: users state a pattern by
+ * listing its edges). An embedding is an injective map m: V_P -> V with
+ * (m(u), m(v)) in E for every pattern arc (u, v); further arcs among the
+ * matched nodes are allowed (non-induced). A match is a distinct matched
+ * subgraph, i.e. an orbit of embeddings under Aut(P); results are unique
+ * (Sec. 5.3). By default the library counts/enumerates matches; with
+ * XM_EMBEDDINGS it counts every embedding (= |Aut(P)| x matches).
+ *
+ * Conventions for every entry point:
+ *   - Return value: XM_OK (0) or an XM_E* status. Nothing is thrown across
+ *     the ABI. On error the output arguments are left untouched unless the
+ *     function says otherwise; xm_strerror() names the status and
+ *     xm_last_error() gives a one-line detail for the calling thread.
+ *   - Ownership: handles (xm_graph, xm_plan) belong to the library until
+ *     the matching *_free call. Input arrays are borrowed for the duration
+ *     of the call and copied. Output buffers belong to the caller.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that
+ *     run kernels enqueue them on `stream` and return after the results
+ *     they report have been copied back (they synchronise `stream`).
+ *   - Node ids are int32 in [0, n). Data graphs need fewer than 2^31 arcs
+ *     after deduplication. Counts are 128-bit, returned as (lo, hi) halves.
+ *   - A graph handle owns one set of device scratch buffers; calls that use
+ *     the same graph handle must not overlap in time (serialise them on one
+ *     stream). Different graph handles are independent.
+ */
+#ifndef XM_H
+#define XM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+    XM_OK = 0,
+    XM_EINVAL = 1,    /* bad argument: ids out of range, bad pattern, ... */
+    XM_ENOMEM = 2,    /* host or device allocation failed */
+    XM_EOVERFLOW = 3, /* enumeration buffer too small; *total is still exact */
+    XM_ECUDA = 4,     /* a CUDA runtime call failed (no device, launch error) */
+    XM_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    XM_EBUSY = 6      /* resource in use */
+};
+
+/* ------------------------------------------------------ pattern flags */
+enum {
+    XM_REDUCE = 0,     /* default: plan from the reduced pattern (Alg. 1, Sec. 5.1-5.2) */
+    XM_NO_REDUCE = 1,  /* plan over the original pattern, no reuse of candidate sets
+                          (the "XMiner without reduction" variant of Sec. 6.3) */
+    XM_EMBEDDINGS = 2  /* count every embedding; no symmetry-breaking conditions */
+};
+
+typedef struct xm_graph_s *xm_graph;
+typedef struct xm_plan_s *xm_plan;
+
+/* Name of a status code (static string). */
+const char *xm_strerror(int status);
+
+/* Detail of the last error raised on the calling thread (static per-thread
+ * buffer, "" when none). */
+const char *xm_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int xm_version(void);
+
+/* ------------------------------------------------------------- graphs */
+
+/*
+ * xm_load_graph -- build the data digraph on the current CUDA device.
+ *
+ * Def. 2.1 (digraph); the per-node out_arcs / in_arcs lists that plan
+ * execution reads (Alg. 2, its two initialisation branches).
+ *
+ *   n          number of nodes; ids are [0, n). 1 <= n < 2^31.
+ *   m          number of input arcs (src[i] -> dst[i]), m >= 0.
+ *   src, dst   arc endpoints, m int32 each, host or device memory (detected
+ *              with cudaPointerGetAttributes). Repeated arcs and
+ *              self-loops are dropped.
+ *   flags      reserved, pass 0.
+ *   stream     stream for the uploads.
+ *   out        receives the handle.
+ *
+ * Builds a dual sorted CSR (out-lists and in-lists, each ascending, int32
+ * offsets) on the host and copies it to device memory owned by the handle,
+ * together with the handle's scratch buffers (about 4 bytes per node).
+ * Errors: XM_EINVAL for n/m out of range or an id outside [0, n), or more
+ * than 2^31-1 arcs after deduplication; XM_ENOMEM; XM_ECUDA.
+ */
+int xm_load_graph(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int flags, void *stream,
+                  xm_graph *out);
+
+/* Node count and arc count after deduplication. */
+int xm_graph_info(xm_graph g, int32_t *n, int64_t *m);
+
+/*
+ * Device pointers of the dual CSR (read-only views owned by the handle):
+ * out_off/in_off have n+1 int32 entries, out_adj/in_adj have m.
+ */
+int xm_graph_csr(xm_graph g, const int32_t **out_off, const int32_t **out_adj, const int32_t **in_off,
+                 const int32_t **in_adj);
+
+/* Frees the handle and its device memory. NULL is a no-op. */
+void xm_graph_free(xm_graph g);
+
+/* ----------------------------------------------------------- patterns */
+
+/*
+ * xm_compile_pattern -- host-only pattern compiler.
+ *
+ * Follows Sec. 4 and Sec. 5.1-5.2:
+ *   1. constraint inclusion among pattern edges and vertices (Thm. 2.1,
+ *      Thm. 2.2, the neighbour grouping of Sec. 4.1, closed to a fixpoint);
+ *   2. pattern reduction by the greedy constraint cover of Alg. 1 (start at
+ *      the highest-degree vertex; repeatedly take the adjacent edge of
+ *      highest coverage; mark included edges as covered);
+ *   3. plan generation (Sec. 5.1): a materialisation order of the pattern
+ *      vertices, and for each vertex the lists it intersects (out-lists of
+ *      matched in-neighbours, in-lists of matched out-neighbours), the
+ *      earlier candidate set it reuses (Sec. 5.2), degree thresholds, and
+ *      symmetry-breaking order conditions (Sec. 7 mentions symmetry
+ *      destruction without a mechanism; the library uses the stabiliser-
+ *      chain conditions of Grochow and Kellis, RECOMB 2007).
+ *
+ *   k          pattern vertices, 2 <= k <= 8 (vertices are 0..k-1).
+ *   e          pattern arcs, 1 <= e <= k(k-1).
+ *   psrc, pdst arc endpoints (host memory), e int32 each.
+ *   flags      XM_REDUCE (0) | XM_NO_REDUCE | XM_EMBEDDINGS.
+ *   out        receives the plan handle.
+ * Errors: XM_EINVAL for a self-loop, a repeated arc, an id outside [0, k),
+ * k or e out of range, or a pattern that is not weakly connected.
+ */
+int xm_compile_pattern(int32_t k, int32_t e, const int32_t *psrc, const int32_t *pdst, int flags,
+                       xm_plan *out);
+
+/*
+ * xm_plan_info -- summary of a compiled plan (any pointer may be NULL).
+ *   k         pattern vertices;
+ *   aut_size  |Aut(P)|;
+ *   n_levels  levels of the plan (= k);
+ *   n_reuse   levels whose candidate set starts from an earlier level's
+ *             set (Sec. 5.2 reuse); 0 with XM_NO_REDUCE;
+ *   start     the pattern vertex matched first (Alg. 1 maxDegree).
+ */
+int xm_plan_info(xm_plan p, int32_t *k, int32_t *aut_size, int32_t *n_levels, int32_t *n_reuse,
+                 int32_t *start);
+
+/*
+ * xm_plan_order -- the plan's materialisation order: order[l] is the
+ * pattern vertex matched at level l (k entries, caller-owned).
+ */
+int xm_plan_order(xm_plan p, int32_t *order);
+
+/*
+ * xm_plan_describe -- human-readable plan (levels, operand lists, reuse,
+ * filters, reduction queue), NUL-terminated, truncated to cap bytes.
+ * Returns the length the full text needs (excluding the NUL) or -XM_EINVAL.
+ */
+int xm_plan_describe(xm_plan p, char *buf, int32_t cap);
+
+/*
+ * xm_plan_level -- the flat plan IR record of one level (for inspection and
+ * tests). Level l matches pattern vertex `vertex`; its candidates are the
+ * intersection of the operand lists i < nops: the out-list (op_dir 0) or
+ * in-list (op_dir 1) of the node matched at level op_level[i]. With
+ * reuse >= 1 the operands in bit set reuse_ops may be replaced by level
+ * `reuse`'s stored candidate set (Sec. 5.2). Filters: x > m(j) for bits j of
+ * lo_mask, x < m(j) for hi_mask, x != m(j) for neq_mask; outdeg(x) >=
+ * dout_min and indeg(x) >= din_min. Errors: XM_EINVAL for a bad level.
+ */
+typedef struct {
+    int32_t vertex;
+    int32_t nops;
+    int32_t op_level[7];
+    int32_t op_dir[7];
+    int32_t reuse;
+    uint32_t reuse_ops;
+    int32_t dout_min;
+    int32_t din_min;
+    uint32_t lo_mask;
+    uint32_t hi_mask;
+    uint32_t neq_mask;
+} xm_level_info;
+
+int xm_plan_level(xm_plan p, int32_t level, xm_level_info *out);
+
+/* Frees a plan. NULL is a no-op. */
+void xm_plan_free(xm_plan p);
+
+/* ------------------------------------------------------------- tuning */
+
+/*
+ * Launch parameters of the matcher (0 = library default):
+ *   window           candidate-window capacity per plan level, in node
+ *                    ids (multiple of 32, 64..4096);
+ *   unit             positions of the first level's candidate list handed
+ *                    out as one work unit (1..65536);
+ *   warps_per_block  1..32;
+ *   blocks_per_sm    resident blocks per SM to launch (persistent grid).
+ */
+typedef struct {
+    int32_t window;
+    int32_t unit;
+    int32_t warps_per_block;
+    int32_t blocks_per_sm;
+} xm_tuning;
+
+/* Sets the tuning used by later calls with this plan (copied). */
+int xm_plan_set_tuning(xm_plan p, const xm_tuning *t);
+/* Reads back the effective tuning. */
+int xm_plan_get_tuning(xm_plan p, xm_tuning *t);
+
+/* ------------------------------------------------------------ matching */
+
+/*
+ * xm_count -- number of matches of plan p in graph g (Alg. 2 plan
+ * execution with count-only result generation, Sec. 5.3).
+ * Writes the 128-bit count as (*lo, *hi). Synchronises `stream`.
+ * Errors: XM_EINVAL (NULL handle/output), XM_ECUDA.
+ */
+int xm_count(xm_graph g, xm_plan p, uint64_t *lo, uint64_t *hi, void *stream);
+
+/*
+ * xm_count_range -- as xm_count, restricted to the matches whose start
+ * vertex (xm_plan_info's `start`) is mapped to a node in [root_lo, root_hi)
+ * (Alg. 2 parallelises over the start vertex's candidates). Counts over a
+ * partition of [0, n) add up to xm_count. Ranges are clipped to [0, n).
+ */
+int xm_count_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t *lo, uint64_t *hi,
+                   void *stream);
+
+/*
+ * Work and traffic counters of one instrumented run (xm_count_stats).
+ *   alg_bytes     algorithmic bytes: per list operand 8 B of offsets plus
+ *                 the cheaper of scanning the list or probing it once per
+ *                 driver element (4 B x min(|L|, |C| x ceil(log2(|L|+1)))),
+ *                 plus 8 B per degree check, 16 B per start-node check;
+ *   extensions    partial matches created (descents into a level);
+ *   set_ops       candidate sets computed (level set-ups);
+ *   units         work units executed;
+ *   leaf_elems    driver elements examined at the last level.
+ */
+typedef struct {
+    uint64_t alg_bytes;
+    uint64_t extensions;
+    uint64_t set_ops;
+    uint64_t units;
+    uint64_t leaf_elems;
+    uint64_t reserved[3];
+} xm_stats;
+
+/*
+ * xm_count_stats -- xm_count_range with the counters above (a separately
+ * compiled, slower kernel; for measurement, not for timing).
+ */
+int xm_count_stats(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t *lo, uint64_t *hi,
+                   xm_stats *stats, void *stream);
+
+/*
+ * xm_enumerate -- materialise the matches (Sec. 5.3 result generation).
+ *
+ *   dev_out   caller-owned device buffer of capacity * k int32; match i is
+ *             written at dev_out[i*k .. i*k+k-1] in pattern-vertex order
+ *             (entry v is the node matched to pattern vertex v).
+ *   capacity  number of matches dev_out can hold.
+ *   total     receives the exact number of matches (always).
+ *   written   receives min(total, capacity).
+ * One embedding per match is written (the one meeting the plan's
+ * symmetry-breaking conditions; every embedding with XM_EMBEDDINGS).
+ * The order of matches is unspecified. Returns XM_EOVERFLOW when total >
+ * capacity (the first `capacity` slots are filled, total stays exact).
+ */
+int xm_enumerate(xm_graph g, xm_plan p, int32_t *dev_out, uint64_t capacity, uint64_t *total,
+                 uint64_t *written, void *stream);
+
+/* xm_enumerate restricted to start nodes in [root_lo, root_hi). */
+int xm_enumerate_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, int32_t *dev_out,
+                       uint64_t capacity, uint64_t *total, uint64_t *written, void *stream);
+
+/*
+ * xm_graph_last_timing -- device time of the last count/enumerate call on
+ * this graph handle, from CUDA events recorded on the call's stream around
+ * its kernels: *prep_ms covers the work-unit count and scan kernels,
+ * *match_ms the persistent matcher kernel. Either pointer may be NULL.
+ * Errors: XM_EINVAL (no call yet), XM_ECUDA.
+ */
+int xm_graph_last_timing(xm_graph g, float *prep_ms, float *match_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XM_H */

@@ -1,0 +1,253 @@
+"""Python binding of the B300 directed subgraph matcher (libxm.so).
+
+Argument marshalling only: every step of matching runs in the CUDA library
+behind the C ABI of include/xm.h (graph build and pattern compilation run
+in its host C++ code). PyTorch supplies device memory and streams.
+
+The library must have been built in-tree (``python -m
+paper_2404_11105_b300.build``); the first call into this package raises
+when it is missing -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libxm.so")
+
+XM_OK, XM_EINVAL, XM_ENOMEM, XM_EOVERFLOW, XM_ECUDA, XM_ETIMEOUT, XM_EBUSY = range(7)
+XM_REDUCE, XM_NO_REDUCE, XM_EMBEDDINGS = 0, 1, 2
+
+# every symbol include/xm.h declares
+EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_graph_info", "xm_graph_csr",
+           "xm_graph_free", "xm_compile_pattern", "xm_plan_info", "xm_plan_order", "xm_plan_level",
+           "xm_plan_describe", "xm_plan_free", "xm_plan_set_tuning", "xm_plan_get_tuning", "xm_count",
+           "xm_count_range", "xm_count_stats", "xm_enumerate", "xm_enumerate_range", "xm_graph_last_timing"]
+
+
+class XmError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        self.status = status
+        super().__init__(f"{lib().xm_strerror(status).decode()}: {detail}")
+
+
+class xm_tuning(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int32), ("unit", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
+class xm_stats(ctypes.Structure):
+    _fields_ = [("alg_bytes", ctypes.c_uint64), ("extensions", ctypes.c_uint64), ("set_ops", ctypes.c_uint64),
+                ("units", ctypes.c_uint64), ("leaf_elems", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 3)]
+
+
+class xm_level_info(ctypes.Structure):
+    _fields_ = [("vertex", ctypes.c_int32), ("nops", ctypes.c_int32), ("op_level", ctypes.c_int32 * 7),
+                ("op_dir", ctypes.c_int32 * 7), ("reuse", ctypes.c_int32), ("reuse_ops", ctypes.c_uint32),
+                ("dout_min", ctypes.c_int32), ("din_min", ctypes.c_int32), ("lo_mask", ctypes.c_uint32),
+                ("hi_mask", ctypes.c_uint32), ("neq_mask", ctypes.c_uint32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2404_11105_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "xm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "xm_last_error": (ctypes.c_char_p, []),
+        "xm_version": (ctypes.c_int, []),
+        "xm_load_graph": (ctypes.c_int, [i32, i64, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "xm_graph_info": (ctypes.c_int, [vp, i32p, ctypes.POINTER(i64)]),
+        "xm_graph_csr": (ctypes.c_int, [vp] + [ctypes.POINTER(vp)] * 4),
+        "xm_graph_free": (None, [vp]),
+        "xm_compile_pattern": (ctypes.c_int, [i32, i32, i32p, i32p, ctypes.c_int, ctypes.POINTER(vp)]),
+        "xm_plan_info": (ctypes.c_int, [vp, i32p, i32p, i32p, i32p, i32p]),
+        "xm_plan_order": (ctypes.c_int, [vp, i32p]),
+        "xm_plan_level": (ctypes.c_int, [vp, i32, ctypes.POINTER(xm_level_info)]),
+        "xm_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, i32]),
+        "xm_plan_free": (None, [vp]),
+        "xm_plan_set_tuning": (ctypes.c_int, [vp, ctypes.POINTER(xm_tuning)]),
+        "xm_plan_get_tuning": (ctypes.c_int, [vp, ctypes.POINTER(xm_tuning)]),
+        "xm_count": (ctypes.c_int, [vp, vp, u64p, u64p, vp]),
+        "xm_count_range": (ctypes.c_int, [vp, vp, i64, i64, u64p, u64p, vp]),
+        "xm_count_stats": (ctypes.c_int, [vp, vp, i64, i64, u64p, u64p, ctypes.POINTER(xm_stats), vp]),
+        "xm_enumerate": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, u64p, u64p, vp]),
+        "xm_enumerate_range": (ctypes.c_int, [vp, vp, i64, i64, vp, ctypes.c_uint64, u64p, u64p, vp]),
+        "xm_graph_last_timing": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libxm.so (ctypes); raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def _check(rc: int):
+    if rc != XM_OK:
+        raise XmError(rc, lib().xm_last_error().decode())
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _ptr(x):
+    """Pointer of a numpy array (host) or a torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.int32 and x.flags.c_contiguous
+        return ctypes.c_void_p(x.ctypes.data)
+    assert str(x.dtype) == "torch.int32" and x.is_contiguous()
+    return ctypes.c_void_p(x.data_ptr())
+
+
+class Graph:
+    """Data digraph resident on the current CUDA device (dual sorted CSR)."""
+
+    def __init__(self, n: int, src, dst, stream=None):
+        h = ctypes.c_void_p()
+        self._keep = (src, dst)
+        _check(lib().xm_load_graph(int(n), len(src), _ptr(src), _ptr(dst), 0, _stream(stream), ctypes.byref(h)))
+        self._keep = None
+        self._h = h
+        n_ = ctypes.c_int32()
+        m_ = ctypes.c_int64()
+        _check(lib().xm_graph_info(h, ctypes.byref(n_), ctypes.byref(m_)))
+        self.n, self.m = n_.value, m_.value
+
+    def csr_pointers(self):
+        ps = [ctypes.c_void_p() for _ in range(4)]
+        _check(lib().xm_graph_csr(self._h, *[ctypes.byref(p) for p in ps]))
+        return [p.value for p in ps]
+
+    def last_timing(self):
+        """(prep_ms, match_ms) of the last call, from CUDA events on its stream."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        _check(lib().xm_graph_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().xm_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Compiled pattern (host-only)."""
+
+    def __init__(self, pattern, flags: int = XM_REDUCE):
+        k, arcs = pattern
+        ps = (ctypes.c_int32 * len(arcs))(*[a for a, _ in arcs])
+        pd = (ctypes.c_int32 * len(arcs))(*[b for _, b in arcs])
+        h = ctypes.c_void_p()
+        _check(lib().xm_compile_pattern(k, len(arcs), ps, pd, flags, ctypes.byref(h)))
+        self._h = h
+        self.pattern = (k, list(arcs))
+        self.flags = flags
+        vals = [ctypes.c_int32() for _ in range(5)]
+        _check(lib().xm_plan_info(h, *[ctypes.byref(v) for v in vals]))
+        self.k, self.aut_size, self.n_levels, self.n_reuse, self.start = [v.value for v in vals]
+
+    def order(self):
+        o = (ctypes.c_int32 * self.k)()
+        _check(lib().xm_plan_order(self._h, o))
+        return list(o)
+
+    def level(self, l: int) -> dict:
+        info = xm_level_info()
+        _check(lib().xm_plan_level(self._h, l, ctypes.byref(info)))
+        return {"vertex": info.vertex, "ops": [(info.op_level[i], info.op_dir[i]) for i in range(info.nops)],
+                "reuse": info.reuse, "reuse_ops": info.reuse_ops, "dout_min": info.dout_min,
+                "din_min": info.din_min, "lo_mask": info.lo_mask, "hi_mask": info.hi_mask,
+                "neq_mask": info.neq_mask}
+
+    def describe(self) -> str:
+        need = lib().xm_plan_describe(self._h, None, 0)
+        buf = ctypes.create_string_buffer(need + 1)
+        lib().xm_plan_describe(self._h, buf, need + 1)
+        return buf.value.decode()
+
+    def set_tuning(self, window=0, unit=0, warps_per_block=0, blocks_per_sm=0):
+        t = xm_tuning(window, unit, warps_per_block, blocks_per_sm)
+        _check(lib().xm_plan_set_tuning(self._h, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        t = xm_tuning()
+        _check(lib().xm_plan_get_tuning(self._h, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in xm_tuning._fields_}
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().xm_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def xm_count(g: Graph, p: Plan, stream=None) -> int:
+    lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().xm_count(g._h, p._h, ctypes.byref(lo), ctypes.byref(hi), _stream(stream)))
+    return (hi.value << 64) | lo.value
+
+
+def xm_count_range(g: Graph, p: Plan, root_lo: int, root_hi: int, stream=None) -> int:
+    lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().xm_count_range(g._h, p._h, root_lo, root_hi, ctypes.byref(lo), ctypes.byref(hi), _stream(stream)))
+    return (hi.value << 64) | lo.value
+
+
+def xm_count_stats(g: Graph, p: Plan, root_lo: int = 0, root_hi: int | None = None, stream=None):
+    lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
+    st = xm_stats()
+    root_hi = g.n if root_hi is None else root_hi
+    _check(lib().xm_count_stats(g._h, p._h, root_lo, root_hi, ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(st),
+                               _stream(stream)))
+    return (hi.value << 64) | lo.value, {f: getattr(st, f) for f, _ in xm_stats._fields_ if f != "reserved"}
+
+
+def xm_enumerate(g: Graph, p: Plan, out, capacity: int | None = None, root_lo: int = 0, root_hi: int | None = None,
+                 stream=None):
+    """Writes matches into the int32 device tensor `out` (capacity * k
+    entries). Returns (total, written); total is exact even on overflow."""
+    cap = out.numel() // p.k if capacity is None else capacity
+    assert out.numel() >= cap * p.k
+    total, written = ctypes.c_uint64(), ctypes.c_uint64()
+    root_hi = g.n if root_hi is None else root_hi
+    rc = lib().xm_enumerate_range(g._h, p._h, root_lo, root_hi, _ptr(out), cap, ctypes.byref(total),
+                                 ctypes.byref(written), _stream(stream))
+    if rc not in (XM_OK, XM_EOVERFLOW):
+        _check(rc)
+    return total.value, written.value, rc == XM_EOVERFLOW

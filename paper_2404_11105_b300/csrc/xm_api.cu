@@ -1,0 +1,363 @@
+// C ABI of the matcher library: graph loading, pattern compilation, and the
+// count / enumerate entry points declared in include/xm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "xm_internal.h"
+#include "xm_kernels.cuh"
+
+namespace xm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static int cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return XM_ECUDA;
+}
+
+#define XM_CUDA(call, what)                        \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+static const xm_tuning kDefaultTuning = {512, 32, 8, 0};
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static void free_graph(xm_graph_s* g) {
+    if (!g) return;
+    cudaFree(g->d_out_off);
+    cudaFree(g->d_out_adj);
+    cudaFree(g->d_in_off);
+    cudaFree(g->d_in_adj);
+    cudaFree(g->d_units);
+    cudaFree(g->d_block_sums);
+    cudaFree(g->d_ctl);
+    for (auto& e : g->ev)
+        if (e) cudaEventDestroy(e);
+    delete g;
+}
+
+// control block: CTL_WORDS words, then a device copy of the plan
+static size_t ctl_bytes() { return CTL_WORDS * sizeof(unsigned long long) + ((sizeof(XmPlanDev) + 255) & ~size_t(255)); }
+
+static XmPlanDev* ctl_plan(xm_graph_s* g) {
+    return reinterpret_cast<XmPlanDev*>(reinterpret_cast<unsigned char*>(g->d_ctl) + CTL_WORDS * sizeof(unsigned long long));
+}
+
+static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int32_t* out, uint64_t capacity,
+               uint64_t* lo, uint64_t* hi, xm_stats* stats, uint64_t* written, cudaStream_t stream) {
+    if (!g || !p || !lo || !hi) { set_error("NULL argument"); return XM_EINVAL; }
+    if (mode == MODE_EMIT && capacity > 0 && !out) { set_error("NULL output buffer"); return XM_EINVAL; }
+    int cur = -1;
+    XM_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+    if (cur != g->device) { set_error("graph lives on another device than the current one"); return XM_EINVAL; }
+    const xm::Plan& P = p->plan;
+    const xm_tuning& t = p->tuning;
+    r_lo = std::max<int64_t>(r_lo, 0);
+    r_hi = std::min<int64_t>(r_hi, g->n);
+    RunArgs a;
+    a.g = {g->d_out_off, g->d_out_adj, g->d_in_off, g->d_in_adj, g->n};
+    a.units = g->d_units;
+    a.block_sums = g->d_block_sums;
+    a.ctl = g->d_ctl;
+    a.r_lo = (int32_t)std::min<int64_t>(r_lo, g->n);
+    a.r_hi = (int32_t)std::max<int64_t>(r_hi, a.r_lo);
+    a.unit = t.unit;
+    a.window = t.window;
+    a.out = out;
+    a.capacity = capacity;
+    XM_CUDA(cudaMemsetAsync(g->d_ctl, 0, CTL_WORDS * sizeof(unsigned long long), stream), "cudaMemsetAsync");
+    XM_CUDA(cudaMemcpyAsync(ctl_plan(g), &P.dev, sizeof(XmPlanDev), cudaMemcpyHostToDevice, stream),
+            "plan upload");
+    cudaError_t e = launch_match(mode, P.dev, ctl_plan(g), a, t.warps_per_block, t.blocks_per_sm, g->n_blocks, stream,
+                                 g->ev);
+    if (e != cudaSuccess) return cuda_fail(e, "matcher launch");
+    g->timed = true;
+    unsigned long long ctl[CTL_WORDS];
+    XM_CUDA(cudaMemcpyAsync(ctl, g->d_ctl, sizeof ctl, cudaMemcpyDeviceToHost, stream), "result readback");
+    XM_CUDA(cudaStreamSynchronize(stream), "matcher execution");
+    if (ctl[CTL_STATUS]) { set_error("work-unit count exceeds 2^31-1 (raise the unit size)"); return XM_EINVAL; }
+    if (mode == MODE_EMIT) {
+        *lo = ctl[CTL_EMIT];
+        *hi = 0;
+        if (written) *written = std::min<uint64_t>(ctl[CTL_EMIT], capacity);
+    } else {
+        *lo = ctl[CTL_COUNT_LO];
+        *hi = ctl[CTL_COUNT_HI];
+    }
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->alg_bytes = ctl[CTL_STATS + 0];
+        stats->extensions = ctl[CTL_STATS + 1];
+        stats->set_ops = ctl[CTL_STATS + 2];
+        stats->units = ctl[CTL_STATS + 3];
+        stats->leaf_elems = ctl[CTL_STATS + 4];
+        // start-node degree checks: 16 B per node in range
+        stats->alg_bytes += 16ull * (uint64_t)(a.r_hi - a.r_lo);
+    }
+    if (mode == MODE_EMIT && ctl[CTL_EMIT] > capacity) {
+        set_error("enumeration buffer too small");
+        return XM_EOVERFLOW;
+    }
+    return XM_OK;
+}
+
+}  // namespace xm
+
+using namespace xm;
+
+extern "C" {
+
+const char* xm_strerror(int status) {
+    switch (status) {
+        case XM_OK: return "XM_OK";
+        case XM_EINVAL: return "XM_EINVAL";
+        case XM_ENOMEM: return "XM_ENOMEM";
+        case XM_EOVERFLOW: return "XM_EOVERFLOW";
+        case XM_ECUDA: return "XM_ECUDA";
+        case XM_ETIMEOUT: return "XM_ETIMEOUT";
+        case XM_EBUSY: return "XM_EBUSY";
+        default: return "XM_UNKNOWN";
+    }
+}
+
+const char* xm_last_error(void) { return g_last_error.c_str(); }
+
+int xm_version(void) { return 100; }
+
+int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, int flags, void* stream_,
+                  xm_graph* out) {
+    if (!out) { set_error("NULL output handle"); return XM_EINVAL; }
+    if (flags != 0) { set_error("flags must be 0"); return XM_EINVAL; }
+    if (n < 1 || m < 0) { set_error("n must be >= 1 and m >= 0"); return XM_EINVAL; }
+    cudaStream_t stream = (cudaStream_t)stream_;
+    std::vector<int32_t> hs, hd;
+    const int32_t* s = src;
+    const int32_t* d = dst;
+    try {
+        if (m > 0 && (is_device_ptr(src) || is_device_ptr(dst))) {
+            hs.resize(m);
+            hd.resize(m);
+            XM_CUDA(cudaMemcpyAsync(hs.data(), src, m * sizeof(int32_t), cudaMemcpyDefault, stream), "arc copy");
+            XM_CUDA(cudaMemcpyAsync(hd.data(), dst, m * sizeof(int32_t), cudaMemcpyDefault, stream), "arc copy");
+            XM_CUDA(cudaStreamSynchronize(stream), "arc copy");
+            s = hs.data();
+            d = hd.data();
+        }
+        HostCsr H;
+        std::string err;
+        int rc = build_host_csr(n, m, s, d, H, err);
+        if (rc) { set_error(err); return rc; }
+        if ((int64_t)n + H.m >= (int64_t)INT32_MAX) { set_error("n + arcs must stay below 2^31"); return XM_EINVAL; }
+        xm_graph_s* g = new xm_graph_s();
+        g->n = n;
+        g->m = H.m;
+        XM_CUDA(cudaGetDevice(&g->device), "cudaGetDevice");
+        const size_t off_b = ((size_t)n + 1) * sizeof(int32_t);
+        const size_t adj_b = (size_t)std::max<int64_t>(H.m, 1) * sizeof(int32_t);
+        g->n_blocks = ((int64_t)n + 1 + SCAN_TILE - 1) / SCAN_TILE;
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_out_off, off_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_in_off, off_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_out_adj, adj_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_in_adj, adj_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_units, off_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_block_sums, g->n_blocks * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_ctl, ctl_bytes());
+        for (auto& ev : g->ev)
+            if (e == cudaSuccess) e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) {
+            free_graph(g);
+            cudaGetLastError();
+            set_error(std::string("device allocation: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA;
+        }
+        const size_t am = (size_t)H.m * sizeof(int32_t);
+        e = cudaMemcpyAsync(g->d_out_off, H.out_off.data(), off_b, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_in_off, H.in_off.data(), off_b, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess && am) e = cudaMemcpyAsync(g->d_out_adj, H.out_adj.data(), am, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess && am) e = cudaMemcpyAsync(g->d_in_adj, H.in_adj.data(), am, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            free_graph(g);
+            return cuda_fail(e, "graph upload");
+        }
+        *out = g;
+        return XM_OK;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return XM_ENOMEM;
+    }
+}
+
+int xm_graph_info(xm_graph g, int32_t* n, int64_t* m) {
+    if (!g) { set_error("NULL graph"); return XM_EINVAL; }
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return XM_OK;
+}
+
+int xm_graph_csr(xm_graph g, const int32_t** out_off, const int32_t** out_adj, const int32_t** in_off,
+                 const int32_t** in_adj) {
+    if (!g) { set_error("NULL graph"); return XM_EINVAL; }
+    if (out_off) *out_off = g->d_out_off;
+    if (out_adj) *out_adj = g->d_out_adj;
+    if (in_off) *in_off = g->d_in_off;
+    if (in_adj) *in_adj = g->d_in_adj;
+    return XM_OK;
+}
+
+void xm_graph_free(xm_graph g) { free_graph(g); }
+
+int xm_graph_last_timing(xm_graph g, float* prep_ms, float* match_ms) {
+    if (!g || !g->timed) { set_error("no timed call on this graph yet"); return XM_EINVAL; }
+    float a = 0, b = 0;
+    XM_CUDA(cudaEventSynchronize(g->ev[2]), "cudaEventSynchronize");
+    XM_CUDA(cudaEventElapsedTime(&a, g->ev[0], g->ev[1]), "cudaEventElapsedTime");
+    XM_CUDA(cudaEventElapsedTime(&b, g->ev[1], g->ev[2]), "cudaEventElapsedTime");
+    if (prep_ms) *prep_ms = a;
+    if (match_ms) *match_ms = b;
+    return XM_OK;
+}
+
+int xm_compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pdst, int flags, xm_plan* out) {
+    if (!out) { set_error("NULL output handle"); return XM_EINVAL; }
+    try {
+        xm_plan_s* p = new xm_plan_s();
+        std::string err;
+        int rc = compile_pattern(k, e, psrc, pdst, flags, p->plan, err);
+        if (rc) {
+            delete p;
+            set_error(err);
+            return rc;
+        }
+        p->tuning = kDefaultTuning;
+        *out = p;
+        return XM_OK;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return XM_ENOMEM;
+    }
+}
+
+int xm_plan_info(xm_plan p, int32_t* k, int32_t* aut_size, int32_t* n_levels, int32_t* n_reuse, int32_t* start) {
+    if (!p) { set_error("NULL plan"); return XM_EINVAL; }
+    if (k) *k = p->plan.k;
+    if (aut_size) *aut_size = p->plan.aut_size;
+    if (n_levels) *n_levels = p->plan.dev.k;
+    if (n_reuse) *n_reuse = p->plan.n_reuse;
+    if (start) *start = p->plan.start;
+    return XM_OK;
+}
+
+int xm_plan_order(xm_plan p, int32_t* order) {
+    if (!p || !order) { set_error("NULL argument"); return XM_EINVAL; }
+    for (int l = 0; l < p->plan.k; l++) order[l] = p->plan.dev.order[l];
+    return XM_OK;
+}
+
+int xm_plan_level(xm_plan p, int32_t level, xm_level_info* out) {
+    if (!p || !out) { set_error("NULL argument"); return XM_EINVAL; }
+    if (level < 0 || level >= p->plan.k) { set_error("level out of range"); return XM_EINVAL; }
+    const XmLevel& L = p->plan.dev.lv[level];
+    memset(out, 0, sizeof *out);
+    out->vertex = p->plan.dev.order[level];
+    out->nops = L.nops;
+    for (int i = 0; i < L.nops; i++) {
+        out->op_level[i] = L.op_level[i];
+        out->op_dir[i] = L.op_dir[i];
+    }
+    out->reuse = L.reuse;
+    out->reuse_ops = L.reuse_ops;
+    out->dout_min = L.dout_min;
+    out->din_min = L.din_min;
+    out->lo_mask = L.lo_mask;
+    out->hi_mask = L.hi_mask;
+    out->neq_mask = L.neq_mask;
+    return XM_OK;
+}
+
+int xm_plan_describe(xm_plan p, char* buf, int32_t cap) {
+    if (!p) { set_error("NULL plan"); return -XM_EINVAL; }
+    std::string s = describe_plan(p->plan);
+    if (buf && cap > 0) {
+        size_t nb = std::min<size_t>(s.size(), (size_t)cap - 1);
+        memcpy(buf, s.data(), nb);
+        buf[nb] = 0;
+    }
+    return (int)s.size();
+}
+
+void xm_plan_free(xm_plan p) { delete p; }
+
+int xm_plan_set_tuning(xm_plan p, const xm_tuning* t) {
+    if (!p || !t) { set_error("NULL argument"); return XM_EINVAL; }
+    xm_tuning v = *t;
+    if (v.window == 0) v.window = kDefaultTuning.window;
+    if (v.unit == 0) v.unit = kDefaultTuning.unit;
+    if (v.warps_per_block == 0) v.warps_per_block = kDefaultTuning.warps_per_block;
+    if (v.window < 64 || v.window > 4096 || (v.window & 31)) { set_error("window must be a multiple of 32 in [64, 4096]"); return XM_EINVAL; }
+    if (v.unit < 1 || v.unit > 65536) { set_error("unit must be in [1, 65536]"); return XM_EINVAL; }
+    if (v.warps_per_block < 1 || v.warps_per_block > 16) { set_error("warps_per_block must be in [1, 16]"); return XM_EINVAL; }
+    if (v.blocks_per_sm < 0 || v.blocks_per_sm > 64) { set_error("blocks_per_sm must be in [0, 64]"); return XM_EINVAL; }
+    p->tuning = v;
+    return XM_OK;
+}
+
+int xm_plan_get_tuning(xm_plan p, xm_tuning* t) {
+    if (!p || !t) { set_error("NULL argument"); return XM_EINVAL; }
+    *t = p->tuning;
+    return XM_OK;
+}
+
+int xm_count(xm_graph g, xm_plan p, uint64_t* lo, uint64_t* hi, void* stream) {
+    return run(g, p, MODE_COUNT, 0, INT32_MAX, nullptr, 0, lo, hi, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int xm_count_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t* lo, uint64_t* hi,
+                   void* stream) {
+    return run(g, p, MODE_COUNT, root_lo, root_hi, nullptr, 0, lo, hi, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int xm_count_stats(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t* lo, uint64_t* hi,
+                   xm_stats* stats, void* stream) {
+    if (!stats) { set_error("NULL stats"); return XM_EINVAL; }
+    return run(g, p, MODE_STATS, root_lo, root_hi, nullptr, 0, lo, hi, stats, nullptr, (cudaStream_t)stream);
+}
+
+int xm_enumerate_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, int32_t* dev_out,
+                       uint64_t capacity, uint64_t* total, uint64_t* written, void* stream) {
+    if (!total || !written) { set_error("NULL output"); return XM_EINVAL; }
+    uint64_t lo = 0, hi = 0, w = 0;
+    int rc = run(g, p, MODE_EMIT, root_lo, root_hi, dev_out, capacity, &lo, &hi, nullptr, &w, (cudaStream_t)stream);
+    if (rc == XM_OK || rc == XM_EOVERFLOW) {
+        *total = lo;
+        *written = w;
+    }
+    return rc;
+}
+
+int xm_enumerate(xm_graph g, xm_plan p, int32_t* dev_out, uint64_t capacity, uint64_t* total, uint64_t* written,
+                 void* stream) {
+    return xm_enumerate_range(g, p, 0, INT32_MAX, dev_out, capacity, total, written, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,456 @@
+// Host-side pattern compiler: constraint inclusion (Sec. 4.1), pattern
+// reduction (Alg. 1), plan generation (Sec. 5.1) with candidate-set reuse
+// (Sec. 5.2), symmetry-breaking conditions, lowered to the flat plan IR.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "xm_internal.h"
+
+namespace xm {
+
+namespace {
+
+struct Pat {
+    int k = 0, e = 0;
+    std::vector<int> s, d;  // arc i: s[i] -> d[i]
+    uint32_t outb[XM_MAXK] = {0}, inb[XM_MAXK] = {0};
+    int dout[XM_MAXK] = {0}, din[XM_MAXK] = {0}, deg[XM_MAXK] = {0};
+    bool arc(int u, int v) const { return (outb[u] >> v) & 1u; }
+    bool incident(int ed, int v) const { return s[ed] == v || d[ed] == v; }
+    int other(int ed, int v) const { return s[ed] == v ? d[ed] : s[ed]; }
+};
+
+inline uint64_t bit(int i) { return 1ull << i; }
+inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+// ------------------------------------------------------------ Aut(P) ---
+
+void automorphisms(const Pat& P, std::vector<std::vector<int>>& out) {
+    std::vector<int> p(P.k);
+    for (int i = 0; i < P.k; i++) p[i] = i;
+    do {
+        bool ok = true;
+        for (int i = 0; i < P.e && ok; i++) ok = P.arc(p[P.s[i]], p[P.d[i]]);
+        if (ok) out.push_back(p);
+    } while (std::next_permutation(p.begin(), p.end()));
+}
+
+// ------------------------------------------- constraint inclusion (4.1) ---
+// incl[e] = set of edges e' with e' included in e (the matches of e' are a
+// subset of those of e under the shared context). Only the degree is a
+// vertex constraint, so a vertex with a larger pattern degree is the more
+// constrained one: x is included in y (same context) when deg(x) >= deg(y).
+
+std::vector<uint64_t> inclusion_sets(const Pat& P) {
+    std::vector<uint64_t> incl(P.e, 0);
+    // Neighbour grouping (Thm. 2.1): edges sharing a destination are
+    // related through their sources, edges sharing a source through their
+    // destinations.
+    for (int a = 0; a < P.e; a++)
+        for (int b = 0; b < P.e; b++) {
+            if (a == b) continue;
+            if (P.d[a] == P.d[b] && P.deg[P.s[a]] >= P.deg[P.s[b]]) incl[b] |= bit(a);
+            if (P.s[a] == P.s[b] && P.deg[P.d[a]] >= P.deg[P.d[b]]) incl[b] |= bit(a);
+        }
+    // Path closure (Thm. 2.2): if e1 is included in e3, an edge e2 that
+    // continues e1 is included in an edge e4 that continues e3 the same way
+    // (leaving the heads, or entering the tails), when e2's far endpoint is
+    // at least as constrained. Repeat to a fixpoint.
+    bool changed = true;
+    while (changed) {
+        changed = false;
+        for (int e3 = 0; e3 < P.e; e3++)
+            for (int e1 = 0; e1 < P.e; e1++) {
+                if (!(incl[e3] & bit(e1))) continue;
+                for (int e2 = 0; e2 < P.e; e2++)
+                    for (int e4 = 0; e4 < P.e; e4++) {
+                        if (e2 == e4 || (incl[e4] & bit(e2))) continue;
+                        bool fwd = P.s[e2] == P.d[e1] && P.s[e4] == P.d[e3] && P.deg[P.d[e2]] >= P.deg[P.d[e4]];
+                        bool bwd = P.d[e2] == P.s[e1] && P.d[e4] == P.s[e3] && P.deg[P.s[e2]] >= P.deg[P.s[e4]];
+                        if (fwd || bwd) { incl[e4] |= bit(e2); changed = true; }
+                    }
+            }
+    }
+    return incl;
+}
+
+// --------------------------------------------------- reduction (Alg. 1) ---
+
+struct Reduction {
+    int start = 0;
+    std::vector<int> split;       // explored edges, in order
+    std::vector<int> covered_by;  // per edge: the edge that covers it, or -1
+    std::vector<int> from;        // per split edge: the vertex it was explored from
+};
+
+struct Reducer {
+    const Pat& P;
+    const std::vector<uint64_t>& incl;
+    bool reduce;
+    uint64_t unvisited;
+    Reduction R;
+
+    Reducer(const Pat& p, const std::vector<uint64_t>& in, bool red) : P(p), incl(in), reduce(red) {
+        unvisited = (P.e == 64) ? ~0ull : (bit(P.e) - 1);
+        R.covered_by.assign(P.e, -1);
+        R.from.assign(P.e, -1);
+    }
+
+    bool has_unvisited_at(int v) const {
+        for (int ed = 0; ed < P.e; ed++)
+            if ((unvisited & bit(ed)) && P.incident(ed, v)) return true;
+        return false;
+    }
+
+    // findMaxECoverage: the unvisited edge at v whose inclusion set covers the
+    // most unvisited edges (ties: lowest edge index).
+    int find_max_coverage(int v) const {
+        int best = -1, best_cov = -1;
+        for (int ed = 0; ed < P.e; ed++) {
+            if (!(unvisited & bit(ed)) || !P.incident(ed, v)) continue;
+            int cov = reduce ? popc64(incl[ed] & unvisited) : 0;
+            if (cov > best_cov) { best = ed; best_cov = cov; }
+        }
+        return best;
+    }
+
+    // updateVInclusion: after edge ec (explored from v) materialises w, the
+    // unvisited edges it includes that hang off v the same way (v -> x when
+    // ec = v -> w, x -> v when ec = w -> v) are covered: x is materialised
+    // from w's candidates, and the covering recurses from x.
+    void update_inclusion(int ec, int v) {
+        if (!reduce) return;
+        bool out_of_v = P.s[ec] == v;
+        for (int ed = 0; ed < P.e; ed++) {
+            if (!(unvisited & bit(ed)) || !(incl[ec] & bit(ed))) continue;
+            bool same_role = out_of_v ? (P.s[ed] == v) : (P.d[ed] == v);
+            if (!same_role) continue;
+            unvisited &= ~bit(ed);
+            R.covered_by[ed] = ec;
+            update_inclusion(ed, v);
+        }
+    }
+
+    // Neighbor_MaxDegree: the neighbour of w with the highest degree that
+    // still has unvisited edges (ties: lowest id); -1 when none.
+    int neighbor_max_degree(int w) const {
+        if (w < 0) return -1;
+        int best = -1;
+        for (int x = 0; x < P.k; x++) {
+            if (x == w || !(P.arc(w, x) || P.arc(x, w)) || !has_unvisited_at(x)) continue;
+            if (best < 0 || P.deg[x] > P.deg[best]) best = x;
+        }
+        return best;
+    }
+
+    void search_split(int u) {
+        int v = u;
+        while (v >= 0) {
+            int w = -1;
+            while (has_unvisited_at(v)) {
+                int mec = find_max_coverage(v);
+                unvisited &= ~bit(mec);
+                R.split.push_back(mec);
+                R.from[mec] = v;
+                w = P.other(mec, v);
+                update_inclusion(mec, v);
+            }
+            v = neighbor_max_degree(w);
+        }
+    }
+
+    void run() {
+        int start = 0;
+        for (int v = 1; v < P.k; v++)
+            if (P.deg[v] > P.deg[start]) start = v;  // maxDegree, ties: lowest id
+        R.start = start;
+        search_split(start);
+        while (unvisited) {
+            int ed = __builtin_ctzll(unvisited);
+            int u = (P.deg[P.s[ed]] <= P.deg[P.d[ed]]) ? P.d[ed] : P.s[ed];
+            search_split(u);
+        }
+    }
+};
+
+// -------------------------------------------- plan generation (Sec. 5.1) ---
+// Materialisation order: the start vertex, then the vertices reached by the
+// explored edges in queue order, each followed by the vertices materialised
+// from it through covered edges.
+
+std::vector<int> materialisation_order(const Pat& P, const Reduction& R) {
+    std::vector<int> order{R.start};
+    uint32_t placed = 1u << R.start;
+    std::vector<int> pending(R.split.begin(), R.split.end());
+    auto place_covered = [&](auto&& self, int ed) -> void {
+        for (int c = 0; c < P.e; c++) {
+            if (R.covered_by[c] != ed) continue;
+            for (int x : {P.s[c], P.d[c]})
+                if (!(placed >> x & 1u) && (placed >> P.other(c, x) & 1u)) {
+                    order.push_back(x);
+                    placed |= 1u << x;
+                }
+            self(self, c);
+        }
+    };
+    bool progress = true;
+    while (!pending.empty() && progress) {
+        progress = false;
+        for (size_t i = 0; i < pending.size(); i++) {
+            int ed = pending[i];
+            bool ps = placed >> P.s[ed] & 1u, pd = placed >> P.d[ed] & 1u;
+            if (!ps && !pd) continue;
+            if (!ps || !pd) {
+                int x = ps ? P.d[ed] : P.s[ed];
+                order.push_back(x);
+                placed |= 1u << x;
+            }
+            place_covered(place_covered, ed);
+            pending.erase(pending.begin() + (long)i);
+            progress = true;
+            break;
+        }
+    }
+    // anything left (not reachable through the queue): adjacent, highest degree first
+    while ((int)order.size() < P.k) {
+        int best = -1;
+        for (int x = 0; x < P.k; x++) {
+            if (placed >> x & 1u) continue;
+            if (!((P.outb[x] | P.inb[x]) & placed)) continue;
+            if (best < 0 || P.deg[x] > P.deg[best]) best = x;
+        }
+        order.push_back(best);
+        placed |= 1u << best;
+    }
+    return order;
+}
+
+// ---------------------------------------------- symmetry-breaking conditions
+// Grochow-Kellis: walking the vertices in plan order, require m(v) < m(w)
+// for every other w in v's orbit under the current group, then keep only the
+// stabiliser of v. Exactly one embedding per Aut-orbit satisfies them all.
+// less[v] = bitmask of vertices w with the condition m(v) < m(w).
+
+void symmetry_conditions(int k, const std::vector<int>& order, std::vector<std::vector<int>> G,
+                         uint32_t less[XM_MAXK]) {
+    for (int i = 0; i < k; i++) less[i] = 0;
+    for (int v : order) {
+        if (G.size() <= 1) break;
+        uint32_t orbit = 0;
+        for (auto& g : G) orbit |= 1u << g[v];
+        orbit &= ~(1u << v);
+        less[v] |= orbit;
+        std::vector<std::vector<int>> H;
+        for (auto& g : G)
+            if (g[v] == v) H.push_back(g);
+        G.swap(H);
+    }
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- compile ---
+
+int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pdst, int flags, Plan& out,
+                    std::string& err) {
+    if (k < 2 || k > XM_MAXK) { err = "k must be in [2, 8]"; return XM_EINVAL; }
+    if (e < 1 || e > k * (k - 1)) { err = "arc count out of range"; return XM_EINVAL; }
+    if (!psrc || !pdst) { err = "NULL arc array"; return XM_EINVAL; }
+    if (flags & ~(XM_NO_REDUCE | XM_EMBEDDINGS)) { err = "unknown flag"; return XM_EINVAL; }
+    Pat P;
+    P.k = k;
+    P.e = e;
+    for (int i = 0; i < e; i++) {
+        int u = psrc[i], v = pdst[i];
+        if (u < 0 || u >= k || v < 0 || v >= k) { err = "pattern vertex id out of range"; return XM_EINVAL; }
+        if (u == v) { err = "pattern self-loop"; return XM_EINVAL; }
+        if (P.arc(u, v)) { err = "repeated pattern arc"; return XM_EINVAL; }
+        P.outb[u] |= 1u << v;
+        P.inb[v] |= 1u << u;
+        P.s.push_back(u);
+        P.d.push_back(v);
+    }
+    // weak connectivity
+    uint32_t seen = 1, frontier = 1;
+    while (frontier) {
+        uint32_t nxt = 0;
+        for (int v = 0; v < k; v++)
+            if (frontier >> v & 1u) nxt |= P.outb[v] | P.inb[v];
+        frontier = nxt & ~seen;
+        seen |= nxt;
+    }
+    if (seen != (1u << k) - 1) { err = "pattern is not weakly connected"; return XM_EINVAL; }
+    for (int v = 0; v < k; v++) {
+        P.dout[v] = __builtin_popcount(P.outb[v]);
+        P.din[v] = __builtin_popcount(P.inb[v]);
+        P.deg[v] = P.dout[v] + P.din[v];
+    }
+
+    const bool reduce = !(flags & XM_NO_REDUCE);
+    std::vector<std::vector<int>> aut;
+    automorphisms(P, aut);
+    std::vector<uint64_t> incl = reduce ? inclusion_sets(P) : std::vector<uint64_t>(e, 0);
+    Reducer red(P, incl, reduce);
+    red.run();
+    const Reduction& R = red.R;
+    std::vector<int> order = materialisation_order(P, R);
+
+    uint32_t less[XM_MAXK];
+    if (flags & XM_EMBEDDINGS)
+        for (int i = 0; i < k; i++) less[i] = 0;
+    else
+        symmetry_conditions(k, order, aut, less);
+    // transitive closure of the "<" conditions (used to check reuse bounds)
+    uint32_t lt[XM_MAXK];
+    for (int i = 0; i < k; i++) lt[i] = less[i];
+    for (int it = 0; it < k; it++)
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < k; j++)
+                if (lt[i] >> j & 1u) lt[i] |= lt[j];
+
+    int level_of[XM_MAXK];
+    for (int l = 0; l < k; l++) level_of[order[l]] = l;
+
+    XmPlanDev D;
+    memset(&D, 0, sizeof D);
+    D.k = k;
+    for (int l = 0; l < k; l++) D.order[l] = order[l];
+    int n_reuse = 0;
+    for (int l = 0; l < k; l++) {
+        int v = order[l];
+        XmLevel& L = D.lv[l];
+        L.reuse = -1;
+        L.dout_min = P.dout[v];
+        L.din_min = P.din[v];
+        uint32_t adj_levels = 0;
+        for (int j = 0; j < l; j++) {
+            int u = order[j];
+            if (P.arc(u, v)) { L.op_level[L.nops] = j; L.op_dir[L.nops] = XM_DIR_OUT; L.nops++; adj_levels |= 1u << j; }
+            if (P.arc(v, u)) { L.op_level[L.nops] = j; L.op_dir[L.nops] = XM_DIR_IN; L.nops++; adj_levels |= 1u << j; }
+            if (less[u] >> v & 1u) L.lo_mask |= 1u << j;  // m(u) < m(v)
+            if (less[v] >> u & 1u) L.hi_mask |= 1u << j;  // m(v) < m(u)
+        }
+        if (l > 0 && L.nops == 0) { err = "internal: plan level without an operand list"; return XM_EINVAL; }
+        L.neq_mask = ((1u << l) - 1) & ~adj_levels & ~L.lo_mask & ~L.hi_mask;
+    }
+    // Candidate-set reuse (Sec. 5.2): level l starts from the stored set of an
+    // earlier level r when (i) every operand list of r is also an operand of
+    // l, (ii) the edge joining l to a shared operand is included in the edge
+    // joining r to it (Sec. 4.1 inclusion), (iii) r's order bounds are
+    // implied at l (degree thresholds are reconciled below). Among valid
+    // sources take the most operands, then the nearest level ("initialise
+    // e_i from e_j rather than e_k").
+    if (reduce) {
+        auto edge_index = [&](int a, int b) {
+            for (int i = 0; i < e; i++)
+                if (P.s[i] == a && P.d[i] == b) return i;
+            return -1;
+        };
+        for (int l = 2; l < k; l++) {
+            XmLevel& L = D.lv[l];
+            int v = order[l];
+            int best = -1, best_ops = 0;
+            uint32_t best_mask = 0;
+            for (int r = 1; r < l; r++) {
+                const XmLevel& Rl = D.lv[r];
+                int w = order[r];
+                uint32_t mask = 0;
+                bool subset = true, included = false;
+                for (int i = 0; i < Rl.nops && subset; i++) {
+                    int found = -1;
+                    for (int q = 0; q < L.nops; q++)
+                        if (L.op_level[q] == Rl.op_level[i] && L.op_dir[q] == Rl.op_dir[i]) found = q;
+                    if (found < 0) { subset = false; break; }
+                    mask |= 1u << found;
+                    int u = order[Rl.op_level[i]];
+                    int el = Rl.op_dir[i] == XM_DIR_OUT ? edge_index(u, v) : edge_index(v, u);
+                    int er = Rl.op_dir[i] == XM_DIR_OUT ? edge_index(u, w) : edge_index(w, u);
+                    if (el >= 0 && er >= 0 && (incl[er] & bit(el))) included = true;
+                }
+                if (!subset || !included || Rl.nops == 0) continue;
+                bool bounds_ok = true;
+                for (int j = 0; j < r && bounds_ok; j++) {
+                    int u = order[j];
+                    if ((Rl.lo_mask >> j & 1u) && !(lt[u] >> v & 1u)) bounds_ok = false;
+                    if ((Rl.hi_mask >> j & 1u) && !(lt[v] >> u & 1u)) bounds_ok = false;
+                }
+                if (!bounds_ok) continue;
+                if (Rl.nops > best_ops || (Rl.nops == best_ops && r > best)) {
+                    best = r;
+                    best_ops = Rl.nops;
+                    best_mask = mask;
+                }
+            }
+            if (best >= 0) {
+                L.reuse = best;
+                L.reuse_ops = best_mask;
+                n_reuse++;
+            }
+        }
+        // A reused set must keep every candidate its reusers need, so the
+        // degree filter of a reuse source is weakened to the componentwise
+        // minimum of its own thresholds and its reusers' (the degree filter
+        // only prunes; weakening it never changes results). Walking down the
+        // levels carries the minimum along reuse chains.
+        for (int l = k - 1; l >= 2; l--) {
+            const XmLevel& L = D.lv[l];
+            if (L.reuse < 1) continue;
+            XmLevel& Rl = D.lv[L.reuse];
+            Rl.dout_min = std::min(Rl.dout_min, L.dout_min);
+            Rl.din_min = std::min(Rl.din_min, L.din_min);
+        }
+    }
+
+    out.dev = D;
+    out.k = k;
+    out.e = e;
+    out.flags = flags;
+    out.aut_size = (int)aut.size();
+    out.n_reuse = n_reuse;
+    out.start = R.start;
+    out.split = R.split;
+    out.covered_by = R.covered_by;
+    out.psrc.assign(psrc, psrc + e);
+    out.pdst.assign(pdst, pdst + e);
+    return XM_OK;
+}
+
+std::string describe_plan(const Plan& p) {
+    std::string s;
+    char buf[256];
+    snprintf(buf, sizeof buf, "k=%d e=%d |Aut|=%d start=%d reuse_levels=%d flags=%d\n", p.k, p.e, p.aut_size,
+             p.start, p.n_reuse, p.flags);
+    s += buf;
+    s += "split:";
+    for (int ed : p.split) {
+        snprintf(buf, sizeof buf, " (%d,%d)", p.psrc[ed], p.pdst[ed]);
+        s += buf;
+    }
+    s += "\ncovered:";
+    for (int ed = 0; ed < p.e; ed++)
+        if (p.covered_by[ed] >= 0) {
+            int c = p.covered_by[ed];
+            snprintf(buf, sizeof buf, " (%d,%d)<=(%d,%d)", p.psrc[ed], p.pdst[ed], p.psrc[c], p.pdst[c]);
+            s += buf;
+        }
+    s += "\n";
+    const XmPlanDev& D = p.dev;
+    for (int l = 0; l < D.k; l++) {
+        const XmLevel& L = D.lv[l];
+        snprintf(buf, sizeof buf, "L%d v%d deg>=(%d,%d) ops:", l, D.order[l], L.dout_min, L.din_min);
+        s += buf;
+        for (int i = 0; i < L.nops; i++) {
+            snprintf(buf, sizeof buf, " %s(L%d)", L.op_dir[i] == XM_DIR_OUT ? "out" : "in", L.op_level[i]);
+            s += buf;
+        }
+        snprintf(buf, sizeof buf, " reuse=%d/0x%x lo=0x%x hi=0x%x neq=0x%x\n", L.reuse, L.reuse_ops, L.lo_mask,
+                 L.hi_mask, L.neq_mask);
+        s += buf;
+    }
+    return s;
+}
+
+}  // namespace xm

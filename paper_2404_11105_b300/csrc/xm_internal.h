@@ -1,0 +1,66 @@
+// Internal declarations of the matcher library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/xm.h"
+#include "xm_plan_ir.h"
+
+struct xm_plan_s;
+struct xm_graph_s;
+
+namespace xm {
+
+struct Plan {
+    XmPlanDev dev;
+    int k = 0, e = 0, flags = 0;
+    int aut_size = 1;
+    int n_reuse = 0;
+    int start = 0;
+    std::vector<int> split;
+    std::vector<int> covered_by;
+    std::vector<int32_t> psrc, pdst;
+};
+
+int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pdst, int flags, Plan& out,
+                    std::string& err);
+std::string describe_plan(const Plan& p);
+
+// Host CSR build: dedup, self-loops dropped, ascending lists.
+struct HostCsr {
+    int32_t n = 0;
+    int64_t m = 0;
+    std::vector<int32_t> out_off, out_adj, in_off, in_adj;
+};
+int build_host_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, HostCsr& out, std::string& err);
+
+void set_error(const std::string& msg);
+
+}  // namespace xm
+
+struct xm_plan_s {
+    xm::Plan plan;
+    xm_tuning tuning;
+};
+
+struct xm_graph_s {
+    int32_t n = 0;
+    int64_t m = 0;
+    int device = 0;
+    int32_t* d_out_off = nullptr;
+    int32_t* d_out_adj = nullptr;
+    int32_t* d_in_off = nullptr;
+    int32_t* d_in_adj = nullptr;
+    // scratch: per-node work-unit counts, scanned in place (n + 1 entries),
+    // block partial sums, and a small control block (counters, accumulators)
+    int32_t* d_units = nullptr;
+    int64_t* d_block_sums = nullptr;
+    unsigned long long* d_ctl = nullptr;
+    int64_t n_blocks = 0;
+    // events around the last call's kernels (prep start, match start, match end)
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool timed = false;
+};

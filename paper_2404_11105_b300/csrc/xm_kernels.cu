@@ -1,0 +1,627 @@
+// Device matcher for directed subgraph matching (plan execution, Alg. 2 of
+// the XMiner paper, re-designed for one B300 GPU).
+//
+// Work decomposition. Alg. 2 runs Explore() from every candidate of the
+// start vertex in parallel. Here the candidates of the first plan level
+// (the operand lists of the start node) are cut into work units of `unit`
+// positions; a persistent grid of warps takes units from a global counter
+// (guided self-scheduling), so the heavy start nodes of a power-law graph
+// are spread over many warps. Each warp runs the depth-first Explore()
+// recursion for its unit as an explicit stack of plan levels in shared
+// memory.
+//
+// Per level, the warp builds the candidate set (Alg. 2: A^{e.dest} =
+// A^{e.dest} cap Pi A^e) in chunks into a shared-memory window: lanes take
+// 32 consecutive ids of the shortest operand list (the driver), test each
+// against the other operand lists by binary search, apply the order,
+// injectivity and degree filters, and compact the survivors with
+// __ballot_sync/__popc. A level whose whole candidate set fits in its
+// window is "complete" and can be reused by later levels in place of the
+// operand lists it already intersected (Sec. 5.2). The last level is never
+// materialised: its candidates are counted (Sec. 5.3 count-only result
+// generation) or written out.
+#include <algorithm>
+#include <climits>
+#include <cstddef>
+
+#include "xm_kernels.cuh"
+
+namespace xm {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct ListRef {
+    const int32_t* p;
+    int32_t len;
+    int32_t shared;
+};
+
+struct LvState {
+    const int32_t* drv;
+    const int32_t* probe[XM_MAXOPS];
+    int32_t plo[XM_MAXOPS];
+    int32_t phi[XM_MAXOPS];
+    int32_t drv_shared;
+    int32_t probe_shared;  // bit i: probe i lives in shared memory
+    int32_t nprobe;
+    int32_t c0, c1;        // cut driver range (order bounds applied)
+    int32_t drv_pos, drv_end;
+    int32_t wcnt, wpos, it_hi;
+    int32_t complete;
+    int32_t empty;
+};
+
+struct WarpSmem {
+    LvState st[XM_MAXK];
+    int32_t m[XM_MAXK];
+};
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__device__ __forceinline__ int32_t ld(const int32_t* p, int i, bool shared) {
+    return shared ? p[i] : __ldg(p + i);
+}
+
+// first index in [lo, hi) with p[idx] >= x
+__device__ __forceinline__ int lbound(const int32_t* p, int lo, int hi, int32_t x, bool shared) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (ld(p, mid, shared) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ ListRef op_list(const GraphDev& g, int dir, int32_t v) {
+    if (dir == XM_DIR_OUT) {
+        int b = __ldg(g.out_off + v), e = __ldg(g.out_off + v + 1);
+        return {g.out_adj + b, e - b, 0};
+    }
+    int b = __ldg(g.in_off + v), e = __ldg(g.in_off + v + 1);
+    return {g.in_adj + b, e - b, 0};
+}
+
+// Order bounds of a level: candidates x must satisfy lo < x < hi.
+__device__ __forceinline__ void level_bounds(const XmLevel& L, const int32_t* m, int32_t& lo, int32_t& hi) {
+    lo = -1;
+    hi = INT_MAX;
+    for (uint32_t a = L.lo_mask; a; a &= a - 1) lo = max(lo, m[__ffs(a) - 1]);
+    for (uint32_t b = L.hi_mask; b; b &= b - 1) hi = min(hi, m[__ffs(b) - 1]);
+}
+
+// Operand lists of the first level for start node v, the driver (shortest
+// list, ties to the first operand) and its cut range. Shared by the unit
+// counter and the matcher so both see the same positions.
+__device__ __forceinline__ void first_level_driver(const XmPlanDev& P, const GraphDev& g, int32_t v, ListRef& drv,
+                                                   int& c0, int& c1) {
+    const XmLevel& L = P.lv[1];
+    drv = op_list(g, L.op_dir[0], v);
+    for (int i = 1; i < L.nops; i++) {
+        ListRef r = op_list(g, L.op_dir[i], v);
+        if (r.len < drv.len) drv = r;
+    }
+    int32_t lo = (L.lo_mask & 1u) ? v : -1;
+    int32_t hi = (L.hi_mask & 1u) ? v : INT_MAX;
+    c0 = 0;
+    c1 = drv.len;
+    if (drv.len > 0) {
+        if (lo >= 0) c0 = lbound(drv.p, 0, drv.len, lo + 1, false);
+        if (hi != INT_MAX) c1 = lbound(drv.p, c0, drv.len, hi, false);
+    } else {
+        c1 = 0;
+    }
+}
+
+__device__ __forceinline__ bool passes_degree(const GraphDev& g, int32_t x, int dmin_out, int dmin_in) {
+    if (dmin_out > 0 && __ldg(g.out_off + x + 1) - __ldg(g.out_off + x) < dmin_out) return false;
+    if (dmin_in > 0 && __ldg(g.in_off + x + 1) - __ldg(g.in_off + x) < dmin_in) return false;
+    return true;
+}
+
+__device__ __forceinline__ int ceil_log2p1(int len) {  // ceil(log2(len + 1))
+    return 32 - __clz(len);
+}
+
+// Sets up level l for the partial match in ws.m[0..l-1]: operand lists
+// (or a complete earlier window in their place), driver, probes and the cut
+// of the driver by the order bounds. Returns algorithmic bytes (stats).
+template <int MODE>
+__device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* wins,
+                                          int W, int l, int lane) {
+    const XmLevel& L = P.lv[l];
+    int32_t lo, hi;
+    level_bounds(L, ws.m, lo, hi);
+    ListRef lists[XM_MAXOPS + 1];
+    int cnt = 0;
+    const bool use_reuse = (L.reuse >= 1) && ws.st[L.reuse].complete;
+    if (use_reuse) lists[cnt++] = {wins + (size_t)(L.reuse - 1) * W, ws.st[L.reuse].wcnt, 1};
+    for (int i = 0; i < L.nops; i++) {
+        if (use_reuse && ((L.reuse_ops >> i) & 1u)) continue;
+        lists[cnt++] = op_list(g, L.op_dir[i], ws.m[L.op_level[i]]);
+    }
+    int d = 0;
+    bool empty = false;
+    for (int i = 0; i < cnt; i++) {
+        if (lists[i].len == 0) empty = true;
+        if (lists[i].len < lists[d].len) d = i;
+    }
+    int c0 = 0, c1 = lists[d].len;
+    if (!empty) {
+        if (lo >= 0) c0 = lbound(lists[d].p, 0, c1, lo + 1, lists[d].shared);
+        if (hi != INT_MAX) c1 = lbound(lists[d].p, c0, c1, hi, lists[d].shared);
+    }
+    if (c0 >= c1) empty = true;
+    unsigned long long bytes = 0;
+    if (lane == 0) {
+        LvState& S = ws.st[l];
+        S.drv = lists[d].p;
+        S.drv_shared = lists[d].shared;
+        int np = 0, psh = 0;
+        for (int i = 0; i < cnt; i++) {
+            if (i == d) continue;
+            S.probe[np] = lists[i].p;
+            S.plo[np] = 0;
+            S.phi[np] = lists[i].len;
+            if (lists[i].shared) psh |= 1 << np;
+            np++;
+        }
+        S.nprobe = np;
+        S.probe_shared = psh;
+        S.c0 = c0;
+        S.c1 = empty ? c0 : c1;
+        S.empty = empty;
+        S.complete = 0;
+        S.wcnt = S.wpos = S.it_hi = 0;
+        if (MODE == MODE_STATS) {
+            int run = empty ? 0 : c1 - c0;
+            for (int i = 0; i < cnt; i++) {
+                if (lists[i].shared) continue;
+                bytes += 8;
+                if (empty) continue;
+                if (i == d) bytes += 4ull * run;
+                else bytes += 4ull * min((long long)lists[i].len, (long long)run * ceil_log2p1(lists[i].len));
+            }
+        }
+    }
+    __syncwarp();
+    return bytes;
+}
+
+// Runs the driver range [pos, end) of level l through probes and filters
+// 32 ids at a time. With WINDOW the survivors are compacted into `win`
+// (stopping when fewer than 32 slots are left); otherwise they are counted
+// or emitted. cnt_a/cnt_b count survivors from driver positions < a / < b.
+template <int MODE, bool WINDOW>
+__device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, LvState& S, int l,
+                                         int32_t* win, int W, int lane, bool filter_deg, int a, int b, int& cnt_a,
+                                         int& cnt_b, const RunArgs& ra, unsigned long long& stat_bytes) {
+    const XmLevel& L = P.lv[l];
+    const bool dsh = S.drv_shared;
+    const int np = S.nprobe;
+    int32_t plo[XM_MAXOPS];
+    for (int p = 0; p < np; p++) plo[p] = S.plo[p];
+    int pos = S.drv_pos;
+    const int end = S.drv_end;
+    int wcnt = WINDOW ? S.wcnt : 0;
+    unsigned long long leaf = 0;
+    const int k = P.k;
+    while (pos < end && (!WINDOW || wcnt + 32 <= W)) {
+        const int i = pos + lane;
+        const bool valid = i < end;
+        const int32_t x = valid ? ld(S.drv, i, dsh) : INT_MAX;
+        bool ok = valid;
+        const int last_lane = min(31, end - 1 - pos);
+        for (int p = 0; p < np; p++) {
+            const bool psh = (S.probe_shared >> p) & 1;
+            const int hi = S.phi[p];
+            const int q = lbound(S.probe[p], plo[p], hi, x, psh);
+            ok = ok && q < hi && ld(S.probe[p], q, psh) == x;
+            plo[p] = __shfl_sync(FULL, q, last_lane);
+            if (__ballot_sync(FULL, ok) == 0) break;
+        }
+        if (ok) {
+            for (uint32_t nm = L.neq_mask; nm; nm &= nm - 1)
+                if (x == ws.m[__ffs(nm) - 1]) ok = false;
+        }
+        if (ok && filter_deg) ok = passes_degree(g, x, L.dout_min, L.din_min);
+        const unsigned mask = __ballot_sync(FULL, ok);
+        const int rank = __popc(mask & ((1u << lane) - 1));
+        if (WINDOW) {
+            if (ok) win[wcnt + rank] = x;
+            wcnt += __popc(mask);
+            cnt_a += __popc(__ballot_sync(FULL, ok && i < a));
+            cnt_b += __popc(__ballot_sync(FULL, ok && i < b));
+            if (MODE == MODE_STATS && lane == 0 && filter_deg) stat_bytes += 8ull * min(32, end - pos);
+        } else if (MODE == MODE_EMIT) {
+            const int c = __popc(mask);
+            unsigned long long base = 0;
+            if (lane == 0 && c) base = atomicAdd(ra.ctl + CTL_EMIT, (unsigned long long)c);
+            base = __shfl_sync(FULL, base, 0);
+            if (ok && base + rank < ra.capacity) {
+                int32_t* o = ra.out + (base + rank) * (unsigned long long)k;
+                for (int t = 0; t < l; t++) o[P.order[t]] = ws.m[t];
+                o[P.order[l]] = x;
+            }
+            leaf += c;
+        } else {
+            leaf += __popc(mask);
+        }
+        pos += 32;
+    }
+    if (pos > end) pos = end;
+    __syncwarp();
+    if (lane == 0) {
+        S.drv_pos = pos;
+        for (int p = 0; p < np; p++) S.plo[p] = plo[p];
+        if (WINDOW) S.wcnt = wcnt;
+    }
+    __syncwarp();
+    return leaf;
+}
+
+// Count (or emit) the candidates of the last level l over driver positions
+// [a, b) (b = -1: the whole cut range).
+template <int MODE>
+__device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* wins, int W,
+                                         int l, int lane, int a, int b, const RunArgs& ra,
+                                         unsigned long long& stat_bytes, unsigned long long& leaf_elems) {
+    stat_bytes += setup_level<MODE>(P, g, ws, wins, W, l, lane);
+    LvState& S = ws.st[l];
+    if (S.empty) return 0;
+    int pos = S.c0, end = S.c1;
+    if (b >= 0) {
+        pos = max(pos, a);
+        end = min(end, b);
+    }
+    if (pos >= end) return 0;
+    if (MODE == MODE_STATS && lane == 0) leaf_elems += end - pos;
+    const XmLevel& L = P.lv[l];
+    if (MODE != MODE_EMIT && S.nprobe == 0) {
+        // A single list: its size, minus already matched nodes inside it.
+        unsigned long long c = end - pos;
+        for (uint32_t nm = L.neq_mask; nm; nm &= nm - 1) {
+            const int32_t y = ws.m[__ffs(nm) - 1];
+            const int q = lbound(S.drv, pos, end, y, S.drv_shared);
+            if (q < end && ld(S.drv, q, S.drv_shared) == y) c--;
+        }
+        return lane == 0 ? c : 0;
+    }
+    if (lane == 0) {
+        S.drv_pos = pos;
+        S.drv_end = end;
+    }
+    __syncwarp();
+    int ca = 0, cb = 0;
+    unsigned long long r = scan_level<MODE, false>(P, g, ws, S, l, nullptr, W, lane, false, 0, 0, ca, cb, ra,
+                                                   stat_bytes);
+    return lane == 0 ? r : 0;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(XmPlanDev) / 4); i += blockDim.x)
+        reinterpret_cast<int32_t*>(smem)[i] = reinterpret_cast<const int32_t*>(plan_g)[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int k = P.k;
+    const int W = ra.window;
+    const size_t warp_bytes = align16(sizeof(WarpSmem)) + (size_t)(k > 2 ? k - 2 : 0) * W * sizeof(int32_t);
+    unsigned char* wbase = smem + align16(sizeof(XmPlanDev)) + (size_t)wib * warp_bytes;
+    WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase);
+    int32_t* wins = reinterpret_cast<int32_t*>(wbase + align16(sizeof(WarpSmem)));
+    const GraphDev& g = ra.g;
+    const int n = g.n;
+    const int total = ra.units[n];
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+
+    unsigned long long acc = 0, st_bytes = 0, st_ext = 0, st_sets = 0, st_units = 0, st_leaf = 0;
+    int root = -1;
+    for (;;) {
+        // guided self-scheduling: take a batch proportional to what is left
+        int start = 0, cnt = 0;
+        if (lane == 0) {
+            unsigned long long seen = *((volatile unsigned long long*)(ra.ctl + CTL_HEAD));
+            long long left = (long long)total - (long long)seen;
+            int batch = left > 0 ? (int)min(64ll, max(1ll, left / (8ll * nwarps))) : 1;
+            unsigned long long s = atomicAdd(ra.ctl + CTL_HEAD, (unsigned long long)batch);
+            start = s >= (unsigned long long)total ? total : (int)s;
+            cnt = min(batch, total - start);
+        }
+        start = __shfl_sync(FULL, start, 0);
+        cnt = __shfl_sync(FULL, cnt, 0);
+        if (cnt <= 0) break;
+        for (int u = start; u < start + cnt; u++) {
+            if (root < 0 || u < ra.units[root] || u >= ra.units[root + 1]) {
+                // last node v with units[v] <= u
+                int lo = 0, hi = n;
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (__ldg(ra.units + mid) <= u) lo = mid; else hi = mid;
+                }
+                root = lo;
+            }
+            const int chunk = u - ra.units[root];
+            if (MODE == MODE_STATS) st_units++;
+            // first level: driver positions of this unit
+            ListRef d1;
+            int c0, c1;
+            first_level_driver(P, g, root, d1, c0, c1);
+            const int a = c0 + chunk * ra.unit;
+            const int b = min(c1, a + ra.unit);
+            if (lane == 0) ws.m[0] = root;
+            __syncwarp();
+            if (MODE == MODE_STATS && chunk == 0 && lane == 0) st_bytes += 16;  // start node degree check
+            if (k == 2) {
+                acc += leaf_level<MODE>(P, g, ws, wins, W, 1, lane, a, b, ra, st_bytes, st_leaf);
+                continue;
+            }
+            unsigned long long sb = setup_level<MODE>(P, g, ws, wins, W, 1, lane);
+            if (MODE == MODE_STATS && chunk == 0) st_bytes += sb;
+            if (MODE == MODE_STATS && lane == 0) st_sets++;
+            LvState& S1 = ws.st[1];
+            if (S1.empty) continue;
+            {
+                int ca = 0, cb = 0;
+                unsigned long long dummy = 0;
+                if (S1.c1 - S1.c0 <= W) {
+                    // whole first-level set fits: build it all (reusable), iterate the unit's part
+                    if (lane == 0) { S1.drv_pos = S1.c0; S1.drv_end = S1.c1; }
+                    __syncwarp();
+                    scan_level<MODE, true>(P, g, ws, S1, 1, wins, W, lane, true, a, b, ca, cb, ra, dummy);
+                    if (lane == 0) { S1.complete = 1; S1.wpos = ca; S1.it_hi = cb; }
+                } else {
+                    if (lane == 0) { S1.drv_pos = a; S1.drv_end = b; }
+                    __syncwarp();
+                    scan_level<MODE, true>(P, g, ws, S1, 1, wins, W, lane, true, 0, 0, ca, cb, ra, dummy);
+                    if (lane == 0) { S1.complete = 0; S1.wpos = 0; S1.it_hi = S1.wcnt; }
+                }
+                if (MODE == MODE_STATS && chunk == 0) st_bytes += dummy;
+                __syncwarp();
+            }
+            // depth-first over levels 1 .. k-2; the last level is counted
+            int l = 1;
+            while (l >= 1) {
+                LvState& S = ws.st[l];
+                if (S.wpos >= S.it_hi) {
+                    if (S.complete || S.drv_pos >= S.drv_end) { l--; continue; }
+                    if (lane == 0) { S.wcnt = 0; S.wpos = 0; }
+                    __syncwarp();
+                    int ca = 0, cb = 0;
+                    scan_level<MODE, true>(P, g, ws, S, l, wins + (size_t)(l - 1) * W, W, lane, true, 0, 0, ca, cb,
+                                           ra, st_bytes);
+                    if (lane == 0) S.it_hi = S.wcnt;
+                    __syncwarp();
+                    continue;
+                }
+                const int32_t x = wins[(size_t)(l - 1) * W + S.wpos];
+                __syncwarp();
+                if (lane == 0) { S.wpos++; ws.m[l] = x; }
+                __syncwarp();
+                if (MODE == MODE_STATS && lane == 0) st_ext++;
+                if (l + 1 == k - 1) {
+                    acc += leaf_level<MODE>(P, g, ws, wins, W, l + 1, lane, 0, -1, ra, st_bytes, st_leaf);
+                    if (MODE == MODE_STATS && lane == 0) st_sets++;
+                    continue;
+                }
+                // descend: set up level l+1 and build its first window
+                const int nl = l + 1;
+                st_bytes += setup_level<MODE>(P, g, ws, wins, W, nl, lane);
+                if (MODE == MODE_STATS && lane == 0) st_sets++;
+                LvState& N = ws.st[nl];
+                if (N.empty) continue;
+                if (lane == 0) { N.drv_pos = N.c0; N.drv_end = N.c1; }
+                __syncwarp();
+                int ca = 0, cb = 0;
+                scan_level<MODE, true>(P, g, ws, N, nl, wins + (size_t)(nl - 1) * W, W, lane, true, 0, 0, ca, cb,
+                                       ra, st_bytes);
+                if (lane == 0) {
+                    N.complete = N.drv_pos >= N.drv_end;
+                    N.wpos = 0;
+                    N.it_hi = N.wcnt;
+                }
+                __syncwarp();
+                l = nl;
+            }
+        }
+    }
+    // 128-bit accumulation of the warp's count
+    unsigned long long lo = acc, hi = 0;
+    for (int off = 16; off; off >>= 1) {
+        unsigned long long olo = __shfl_down_sync(FULL, lo, off);
+        unsigned long long ohi = __shfl_down_sync(FULL, hi, off);
+        unsigned long long s = lo + olo;
+        hi += ohi + (s < lo ? 1 : 0);
+        lo = s;
+    }
+    if (lane == 0 && (lo | hi)) {
+        unsigned long long old = atomicAdd(ra.ctl + CTL_COUNT_LO, lo);
+        unsigned long long carry = (old + lo < old) ? 1 : 0;
+        if (hi + carry) atomicAdd(ra.ctl + CTL_COUNT_HI, hi + carry);
+    }
+    if (MODE == MODE_STATS && lane == 0) {
+        atomicAdd(ra.ctl + CTL_STATS + 0, st_bytes);
+        atomicAdd(ra.ctl + CTL_STATS + 1, st_ext);
+        atomicAdd(ra.ctl + CTL_STATS + 2, st_sets);
+        atomicAdd(ra.ctl + CTL_STATS + 3, st_units);
+        atomicAdd(ra.ctl + CTL_STATS + 4, st_leaf);
+    }
+}
+
+// Per start node: number of work units (0 when the node fails the start
+// vertex's degree filter or lies outside [r_lo, r_hi)). units[n] = 0.
+__global__ void k_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+    __shared__ XmPlanDev P;
+    for (int i = threadIdx.x; i < (int)(sizeof(XmPlanDev) / 4); i += blockDim.x)
+        reinterpret_cast<int32_t*>(&P)[i] = reinterpret_cast<const int32_t*>(plan_g)[i];
+    __syncthreads();
+    const GraphDev& g = ra.g;
+    const int n = g.n;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
+        int u = 0;
+        if (v < n && v >= ra.r_lo && v < ra.r_hi && passes_degree(g, v, P.lv[0].dout_min, P.lv[0].din_min)) {
+            ListRef d;
+            int c0, c1;
+            first_level_driver(P, g, v, d, c0, c1);
+            if (c1 > c0) u = (c1 - c0 + ra.unit - 1) / ra.unit;
+        }
+        ra.units[v] = u;
+    }
+}
+
+// Exclusive scan of units[0..n] in place (three passes over tiles).
+__device__ __forceinline__ long long block_sum(long long x) {
+    __shared__ long long wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o; o >>= 1) x += __shfl_down_sync(FULL, x, o);
+    if (lane == 0) wsum[w] = x;
+    __syncthreads();
+    long long t = 0;
+    if (threadIdx.x < 32) {
+        t = (threadIdx.x < (blockDim.x >> 5)) ? wsum[threadIdx.x] : 0;
+        for (int o = 16; o; o >>= 1) t += __shfl_down_sync(FULL, t, o);
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+__global__ void k_scan_reduce(const int32_t* __restrict__ v, int64_t len, int64_t* __restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    long long s = 0;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += blockDim.x)
+        if (base + i < len) s += v[base + i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) sums[blockIdx.x] = s;
+}
+
+// exclusive scan of one tile held as `per` consecutive values per thread
+template <typename T>
+__device__ void block_exclusive_scan(T* vals, int per, T carry_in, T& total) {
+    __shared__ T wtot[32];
+    __shared__ T wpre[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T t = 0;
+    for (int j = 0; j < per; j++) t += vals[j];
+    T inc = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wtot[w] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T run = 0;
+        for (int i = 0; i < nw; i++) { wpre[i] = run; run += wtot[i]; }
+        wtot[0] = run;
+    }
+    __syncthreads();
+    T pre = carry_in + wpre[w] + inc - t;
+    total = wtot[0];
+    for (int j = 0; j < per; j++) {
+        T x = vals[j];
+        vals[j] = pre;
+        pre += x;
+    }
+    __syncthreads();
+}
+
+__global__ void k_scan_top(int64_t* sums, int64_t nb, int32_t* __restrict__ status) {
+    // one block: exclusive scan of the tile sums, several passes of blockDim*8
+    const int per = 8;
+    long long carry = 0;
+    for (int64_t base = 0; base < nb; base += (int64_t)blockDim.x * per) {
+        long long vals[per];
+        for (int j = 0; j < per; j++) {
+            int64_t i = base + (int64_t)threadIdx.x * per + j;
+            vals[j] = i < nb ? sums[i] : 0;
+        }
+        long long tot;
+        block_exclusive_scan<long long>(vals, per, carry, tot);
+        for (int j = 0; j < per; j++) {
+            int64_t i = base + (int64_t)threadIdx.x * per + j;
+            if (i < nb) sums[i] = vals[j];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && carry > INT_MAX) *status = 1;
+}
+
+__global__ void k_scan_down(int32_t* __restrict__ v, int64_t len, const int64_t* __restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    const int per = SCAN_TILE / 1024;  // launched with 1024 threads
+    long long vals[per];
+    for (int j = 0; j < per; j++) {
+        int64_t i = base + (int64_t)threadIdx.x * per + j;
+        vals[j] = i < len ? v[i] : 0;
+    }
+    long long tot;
+    block_exclusive_scan<long long>(vals, per, sums[blockIdx.x], tot);
+    for (int j = 0; j < per; j++) {
+        int64_t i = base + (int64_t)threadIdx.x * per + j;
+        if (i < len) v[i] = (int32_t)vals[j];
+    }
+}
+
+}  // namespace
+
+size_t match_smem_bytes(int k, int window, int warps) {
+    size_t warp_bytes = align16(sizeof(WarpSmem)) + (size_t)(k > 2 ? k - 2 : 0) * window * sizeof(int32_t);
+    return align16(sizeof(XmPlanDev)) + warp_bytes * warps;
+}
+
+static cudaError_t set_smem_attr(const void* fn, size_t bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev, const RunArgs& a,
+                         int warps_per_block, int blocks_per_sm, int64_t n_blocks, cudaStream_t stream,
+                         cudaEvent_t* ev) {
+    cudaError_t err;
+    const int64_t len = (int64_t)a.g.n + 1;
+    int dev = 0, nsm = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if (ev && (err = cudaEventRecord(ev[0], stream)) != cudaSuccess) return err;
+    // 1. units per start node
+    {
+        int64_t blocks = (len + 255) / 256;
+        int grid = (int)std::min<int64_t>(blocks, (int64_t)nsm * 16);
+        k_units<<<grid, 256, 0, stream>>>(plan_dev, a);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    // 2. exclusive scan in place
+    if (n_blocks < (len + SCAN_TILE - 1) / SCAN_TILE) return cudaErrorInvalidValue;
+    const int64_t nb = (len + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_reduce<<<(unsigned)nb, 1024, 0, stream>>>(a.units, len, a.block_sums);
+    k_scan_top<<<1, 1024, 0, stream>>>(a.block_sums, nb, reinterpret_cast<int32_t*>(a.ctl + CTL_STATUS));
+    k_scan_down<<<(unsigned)nb, 1024, 0, stream>>>(a.units, len, a.block_sums);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // 3. persistent matcher
+    const size_t smem = match_smem_bytes(P.k, a.window, warps_per_block);
+    const void* fn = mode == MODE_STATS ? (const void*)k_match<MODE_STATS>
+                     : mode == MODE_EMIT ? (const void*)k_match<MODE_EMIT>
+                                         : (const void*)k_match<MODE_COUNT>;
+    if ((err = set_smem_attr(fn, smem)) != cudaSuccess) return err;
+    int occ = 0;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps_per_block * 32, smem)) != cudaSuccess)
+        return err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, occ) : occ;
+    dim3 grid(nsm * bps), block(warps_per_block * 32);
+    if (ev && (err = cudaEventRecord(ev[1], stream)) != cudaSuccess) return err;
+    if (mode == MODE_STATS)
+        k_match<MODE_STATS><<<grid, block, smem, stream>>>(plan_dev, a);
+    else if (mode == MODE_EMIT)
+        k_match<MODE_EMIT><<<grid, block, smem, stream>>>(plan_dev, a);
+    else
+        k_match<MODE_COUNT><<<grid, block, smem, stream>>>(plan_dev, a);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (ev && (err = cudaEventRecord(ev[2], stream)) != cudaSuccess) return err;
+    return cudaSuccess;
+}
+
+}  // namespace xm

@@ -1,0 +1,49 @@
+// Flat plan IR shared by the host pattern compiler and the device matcher.
+//
+// One record per plan level l = 0..k-1; level l matches pattern vertex
+// order[l]. Level 0 is the start vertex (Alg. 1 maxDegree): its candidates
+// are the nodes passing the degree filter (the "init A^{p.start}" step of
+// Alg. 2). For l >= 1 the candidate set is
+//
+//   C_l = { x in  AND_i L_i  :  x passes the filters of level l }
+//
+// where each operand list L_i is N_out(m_j) (pattern arc order[j] ->
+// order[l]) or N_in(m_j) (pattern arc order[l] -> order[j]) of a node m_j
+// matched at an earlier level j (Alg. 2: A^{e.dest} = A^{e.dest} cap
+// Pi_{e.dest} A^e). With reuse r >= 1, the operand lists flagged in
+// reuse_ops are already intersected in level r's stored candidate set, which
+// is used in their place when it is held complete in shared memory
+// (Sec. 5.2 intermediate-result reuse). Filters:
+//   - order bounds: x > m_j for j in lo_mask, x < m_j for j in hi_mask
+//     (symmetry-breaking conditions);
+//   - injectivity: x != m_j for j in neq_mask (levels not already excluded
+//     by an operand list or an order bound);
+//   - degree: outdeg(x) >= dout_min and indeg(x) >= din_min (vertex
+//     constraint of Sec. 2; skipped at the last level, where it cannot
+//     prune).
+#pragma once
+#include <stdint.h>
+
+#define XM_MAXK 8
+#define XM_MAXOPS 7
+
+enum { XM_DIR_OUT = 0, XM_DIR_IN = 1 };
+
+struct XmLevel {
+    int32_t nops;
+    int32_t op_level[XM_MAXOPS];
+    int32_t op_dir[XM_MAXOPS];
+    int32_t reuse;       // earlier level whose stored set may replace some operands, or -1
+    uint32_t reuse_ops;  // bit i: operand i is already applied in level `reuse`'s set
+    int32_t dout_min;
+    int32_t din_min;
+    uint32_t lo_mask;
+    uint32_t hi_mask;
+    uint32_t neq_mask;
+};
+
+struct XmPlanDev {
+    int32_t k;
+    int32_t order[XM_MAXK];  // pattern vertex of each level
+    XmLevel lv[XM_MAXK];
+};

@@ -1,0 +1,262 @@
+"""GPU parity: the CUDA matcher (through the C ABI) against the CPU oracle.
+
+Counts must be bit-exact; enumerated match sets must be equal after the
+oracle's canonicalisation (each match written once, in any order).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def xm():
+    import paper_2404_11105_b300 as m
+    return m
+
+
+def graph_pair(xm, n, src, dst):
+    return xm.Graph(n, src, dst), oracle.OracleGraph(n, src, dst)
+
+
+TUNINGS = [dict(), dict(window=64, unit=1, warps_per_block=2), dict(window=96, unit=7, warps_per_block=4),
+           dict(window=128, unit=3, warps_per_block=1, blocks_per_sm=1)]
+
+NAMED = {"cycle3": synth.CYCLE3, "ffl": synth.FFL, "bifan": synth.BIFAN, "cycle4": synth.CYCLE4,
+         "biparallel": synth.BIPARALLEL, "ffchain5": synth.FFCHAIN5}
+
+
+def random_patterns(count, seed):
+    pats = []
+    for i in range(count):
+        u = synth.uniforms(seed, 1000 + i, 2)
+        pats.append(synth.random_pattern(3 + int(u[0] * 4), 0.3 + 0.4 * u[1], seed, i))
+    return pats
+
+
+# ------------------------------------------------------- tiny ER (config 0)
+
+@pytest.fixture(scope="module")
+def tiny(xm):
+    n, src, dst = synth.tiny_er()
+    return graph_pair(xm, n, src, dst)
+
+
+@pytest.mark.parametrize("name", ["cycle3", "ffl", "bifan"])
+def test_tiny_counts_and_sets(xm, tiny, name):
+    g, og = tiny
+    pat = NAMED[name]
+    want = og.count_matches(pat)
+    ref_rows = og.enumerate(pat)
+    assert ref_rows.shape[0] == want
+    for flags in (xm.XM_REDUCE, xm.XM_NO_REDUCE):
+        for tun in TUNINGS:
+            p = xm.Plan(pat, flags)
+            p.set_tuning(**tun)
+            assert xm.xm_count(g, p) == want, (flags, tun)
+            out = torch.full((max(want, 1) * pat[0],), -1, dtype=torch.int32, device="cuda")
+            total, written, over = xm.xm_enumerate(g, p, out)
+            assert (total, written, over) == (want, want, False)
+            rows = out[: want * pat[0]].view(-1, pat[0]).cpu().numpy()
+            canon = oracle.canonicalize(pat, rows)
+            assert np.array_equal(canon, ref_rows)
+            # each match written once
+            assert np.unique(canon, axis=0).shape[0] == want
+    pe = xm.Plan(pat, xm.XM_EMBEDDINGS)
+    assert xm.xm_count(g, pe) == og.count_embeddings(pat)
+
+
+@pytest.mark.parametrize("name", sorted(synth.MOTIFS3))
+def test_tiny_motifs(xm, tiny, name):
+    g, og = tiny
+    pat = synth.MOTIFS3[name]
+    want = og.count_matches(pat)
+    for tun in TUNINGS[:2]:
+        p = xm.Plan(pat)
+        p.set_tuning(**tun)
+        assert xm.xm_count(g, p) == want
+
+
+def test_tiny_enumerate_overflow(xm, tiny):
+    g, og = tiny
+    pat = synth.BIFAN
+    want = og.count_matches(pat)
+    cap = max(1, want // 3)
+    p = xm.Plan(pat)
+    out = torch.full((cap * 4,), -1, dtype=torch.int32, device="cuda")
+    total, written, over = xm.xm_enumerate(g, p, out, capacity=cap)
+    assert over and total == want and written == cap
+    rows = oracle.canonicalize(pat, out.view(-1, 4).cpu().numpy())
+    ref = {tuple(r) for r in og.enumerate(pat).tolist()}
+    assert all(tuple(r) in ref for r in rows.tolist())
+    assert np.unique(rows, axis=0).shape[0] == cap
+
+
+# ------------------------------------------ small skewed graphs, many tiles
+
+@pytest.fixture(scope="module")
+def rmat_small(xm):
+    # R-MAT scale 10, edge factor 6: skewed (hubs of a few hundred arcs),
+    # small enough for the single-threaded oracle to finish in seconds
+    n, src, dst = synth.rmat_graph(10, 6, seed=17)
+    return graph_pair(xm, n, src, dst)
+
+
+@pytest.fixture(scope="module")
+def rmat_tiny(xm):
+    # R-MAT scale 9, edge factor 8, for random patterns of up to 6 vertices
+    n, src, dst = synth.rmat_graph(9, 8, seed=17)
+    return graph_pair(xm, n, src, dst)
+
+
+@pytest.mark.parametrize("name", list(NAMED))
+def test_rmat_small_named(xm, rmat_small, name):
+    g, og = rmat_small
+    pat = NAMED[name]
+    want = og.count_matches(pat)
+    for flags in (xm.XM_REDUCE, xm.XM_NO_REDUCE):
+        for tun in TUNINGS:
+            p = xm.Plan(pat, flags)
+            p.set_tuning(**tun)
+            assert xm.xm_count(g, p) == want, (flags, tun)
+    pe = xm.Plan(pat, xm.XM_EMBEDDINGS)
+    assert xm.xm_count(g, pe) == og.count_embeddings(pat)
+
+
+@pytest.mark.parametrize("pattern", random_patterns(16, 5))
+def test_rmat_small_random_patterns(xm, rmat_tiny, pattern):
+    g, og = rmat_tiny
+    want = og.count_matches(pattern)
+    for tun in (TUNINGS[0], TUNINGS[1]):
+        p = xm.Plan(pattern)
+        p.set_tuning(**tun)
+        assert xm.xm_count(g, p) == want
+
+
+def test_root_range_additivity(xm, rmat_small):
+    g, og = rmat_small
+    for pat in (synth.BIFAN, synth.CYCLE4, synth.FFCHAIN5):
+        p = xm.Plan(pat)
+        whole = xm.xm_count(g, p)
+        cuts = [0, 1, 2, 17, 300, 1024, g.n]
+        parts = sum(xm.xm_count_range(g, p, a, b) for a, b in zip(cuts, cuts[1:]))
+        assert parts == whole
+        # per start node, in embeddings mode: the oracle rooted at the plan's start vertex
+        pe = xm.Plan(pat, xm.XM_EMBEDDINGS)
+        for r in (0, 1, 5, 77, 1000):
+            assert xm.xm_count_range(g, pe, r, r + 1) == og.count_embeddings(pat, pe.start, r, r + 1)
+
+
+def test_enumerate_sets_rmat_small(xm, rmat_small):
+    g, og = rmat_small
+    for pat in (synth.FFL, synth.CYCLE4, synth.FFCHAIN5):
+        want = og.count_matches(pat)
+        ref = og.enumerate(pat)
+        p = xm.Plan(pat)
+        p.set_tuning(window=64, unit=5)
+        out = torch.full((max(want, 1) * pat[0],), -1, dtype=torch.int32, device="cuda")
+        total, written, over = xm.xm_enumerate(g, p, out)
+        assert total == want and written == want and not over
+        rows = oracle.canonicalize(pat, out[: want * pat[0]].view(-1, pat[0]).cpu().numpy())
+        assert np.array_equal(rows, ref)
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_edge_cases(xm):
+    # no arcs at all
+    g = xm.Graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert g.m == 0
+    assert xm.xm_count(g, xm.Plan(synth.CYCLE3)) == 0
+    # self-loops and repeats only
+    g = xm.Graph(3, np.array([0, 1, 1, 2, 2], np.int32), np.array([0, 1, 2, 1, 1], np.int32))
+    assert g.m == 2
+    assert xm.xm_count(g, xm.Plan((2, [(0, 1)]))) == 2
+    assert xm.xm_count(g, xm.Plan((2, [(0, 1), (1, 0)]))) == 1
+    # single arc pattern counts arcs; reciprocal pair counts reciprocal pairs
+    n, src, dst = synth.er_graph(500, 6000, seed=9)
+    g, og = graph_pair(xm, n, src, dst)
+    assert xm.xm_count(g, xm.Plan((2, [(0, 1)]))) == og.m
+    assert xm.xm_count(g, xm.Plan((2, [(0, 1), (1, 0)]))) == og.count_matches((2, [(0, 1), (1, 0)]))
+    # empty root range, out-of-range root range
+    p = xm.Plan(synth.FFL)
+    assert xm.xm_count_range(g, p, 10, 10) == 0
+    assert xm.xm_count_range(g, p, n + 5, n + 50) == 0
+    assert xm.xm_count_range(g, p, -100, n + 100) == xm.xm_count(g, p)
+    # enumerate with capacity 0: exact total, overflow flagged
+    out = torch.empty(1, dtype=torch.int32, device="cuda")
+    total, written, over = xm.xm_enumerate(g, p, out, capacity=0)
+    assert total == og.count_matches(synth.FFL) and written == 0 and over == (total > 0)
+    # complete digraph (dense lists, every candidate survives)
+    k7 = [(u, v) for u in range(24) for v in range(24) if u != v]
+    g, og = graph_pair(xm, 24, np.array([a for a, _ in k7], np.int32), np.array([b for _, b in k7], np.int32))
+    for pat in (synth.CYCLE4, synth.BIFAN, synth.FFCHAIN5):
+        assert xm.xm_count(g, xm.Plan(pat)) == og.count_matches(pat)
+
+
+def test_device_pointer_input(xm):
+    n, src, dst = synth.er_graph(800, 9000, seed=12)
+    g1 = xm.Graph(n, src, dst)
+    g2 = xm.Graph(n, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
+    assert g1.m == g2.m
+    p = xm.Plan(synth.BIFAN)
+    assert xm.xm_count(g1, p) == xm.xm_count(g2, p)
+
+
+def test_stats_counters(xm, rmat_small):
+    g, og = rmat_small
+    p = xm.Plan(synth.BIFAN)
+    c, st = xm.xm_count_stats(g, p)
+    assert c == og.count_matches(synth.BIFAN)
+    assert st["alg_bytes"] > 0 and st["units"] > 0 and st["extensions"] > 0
+    prep, match = g.last_timing()
+    assert prep >= 0 and match > 0
+
+
+# ------------------------------------- full-size R-MAT scale 20 (config 1)
+
+@pytest.fixture(scope="module")
+def s20(xm):
+    n, src, dst = synth.rmat20()
+    g = xm.Graph(n, src, dst)
+    og = oracle.OracleGraph(n, src, dst)
+    return g, og
+
+
+def test_s20_motifs_sampled_and_closed_forms(xm, s20):
+    """All 13 motifs at full size in the bench's launch configuration:
+    closed forms where they are cheap (stars, 2-path), and per-start-node
+    embedding counts against the oracle on sampled start nodes (hubs and
+    uniform), plus reduced == unreduced on the whole graph."""
+    g, og = s20
+    off, adj = og.out_csr()
+    outdeg = np.diff(off)
+    indeg = np.bincount(adj, minlength=og.n)
+    # reciprocal partners per node
+    src_of = np.repeat(np.arange(og.n, dtype=np.int64), outdeg)
+    key = src_of * og.n + adj                      # ascending: CSR order
+    rkey = adj.astype(np.int64) * og.n + src_of
+    pos = np.minimum(np.searchsorted(key, rkey), key.size - 1)
+    r = np.bincount(src_of[key[pos] == rkey], minlength=og.n)
+    c2 = lambda x: (x * (x - 1) // 2).sum()
+    assert xm.xm_count(g, xm.Plan(synth.MOTIFS3["021D"])) == int(c2(outdeg.astype(object)))
+    assert xm.xm_count(g, xm.Plan(synth.MOTIFS3["021U"])) == int(c2(indeg.astype(object)))
+    assert xm.xm_count(g, xm.Plan(synth.MOTIFS3["021C"])) == int((indeg.astype(object) * outdeg - r).sum())
+    rng = np.random.default_rng(20)
+    # heavy start nodes the single-threaded oracle still finishes quickly
+    deg = outdeg + indeg
+    heavy = np.nonzero(deg <= 1500)[0]
+    heavy = heavy[np.argsort(-deg[heavy])][:8]
+    roots = np.concatenate([heavy, rng.integers(0, og.n, 24)])
+    for name, pat in synth.MOTIFS3.items():
+        red = xm.xm_count(g, xm.Plan(pat))
+        assert red == xm.xm_count(g, xm.Plan(pat, xm.XM_NO_REDUCE)), name
+        pe = xm.Plan(pat, xm.XM_EMBEDDINGS)
+        for v in roots:
+            v = int(v)
+            assert xm.xm_count_range(g, pe, v, v + 1) == og.count_embeddings(pat, pe.start, v, v + 1), (name, v)
