@@ -47,6 +47,9 @@ static void free_graph(xm_graph_s* g) {
     cudaFree(g->d_out_adj);
     cudaFree(g->d_in_off);
     cudaFree(g->d_in_adj);
+    cudaFree(g->d_root_chunks);
+    cudaFree(g->d_chunk_cnt);
+    cudaFree(g->d_l1set);
     cudaFree(g->d_units);
     cudaFree(g->d_block_sums);
     cudaFree(g->d_ctl);
@@ -75,9 +78,14 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
     r_hi = std::min<int64_t>(r_hi, g->n);
     RunArgs a;
     a.g = {g->d_out_off, g->d_out_adj, g->d_in_off, g->d_in_adj, g->n};
+    a.root_chunks = g->d_root_chunks;
+    a.chunk_cnt = g->d_chunk_cnt;
+    a.l1set = g->d_l1set;
     a.units = g->d_units;
     a.block_sums = g->d_block_sums;
+    a.n_block_sums = g->n_block_sums;
     a.ctl = g->d_ctl;
+    a.cmax = (int32_t)g->cmax;
     a.r_lo = (int32_t)std::min<int64_t>(r_lo, g->n);
     a.r_hi = (int32_t)std::max<int64_t>(r_hi, a.r_lo);
     a.unit = t.unit;
@@ -87,8 +95,7 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
     XM_CUDA(cudaMemsetAsync(g->d_ctl, 0, CTL_WORDS * sizeof(unsigned long long), stream), "cudaMemsetAsync");
     XM_CUDA(cudaMemcpyAsync(ctl_plan(g), &P.dev, sizeof(XmPlanDev), cudaMemcpyHostToDevice, stream),
             "plan upload");
-    cudaError_t e = launch_match(mode, P.dev, ctl_plan(g), a, t.warps_per_block, t.blocks_per_sm, g->n_blocks, stream,
-                                 g->ev);
+    cudaError_t e = launch_match(mode, P.dev, ctl_plan(g), a, t.warps_per_block, t.blocks_per_sm, stream, g->ev);
     if (e != cudaSuccess) return cuda_fail(e, "matcher launch");
     g->timed = true;
     unsigned long long ctl[CTL_WORDS];
@@ -173,14 +180,19 @@ int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, 
         XM_CUDA(cudaGetDevice(&g->device), "cudaGetDevice");
         const size_t off_b = ((size_t)n + 1) * sizeof(int32_t);
         const size_t adj_b = (size_t)std::max<int64_t>(H.m, 1) * sizeof(int32_t);
-        g->n_blocks = ((int64_t)n + 1 + SCAN_TILE - 1) / SCAN_TILE;
+        g->cmax = chunk_capacity(n, H.m);
+        if (g->cmax >= INT32_MAX) { delete g; set_error("graph too large for the chunk index"); return XM_EINVAL; }
+        g->n_block_sums = (std::max<int64_t>((int64_t)n + 1, g->cmax + 1) + SCAN_TILE - 1) / SCAN_TILE;
         cudaError_t e = cudaSuccess;
         if (e == cudaSuccess) e = cudaMalloc(&g->d_out_off, off_b);
         if (e == cudaSuccess) e = cudaMalloc(&g->d_in_off, off_b);
         if (e == cudaSuccess) e = cudaMalloc(&g->d_out_adj, adj_b);
         if (e == cudaSuccess) e = cudaMalloc(&g->d_in_adj, adj_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_root_chunks, off_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_chunk_cnt, (size_t)(g->cmax + 1) * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_l1set, adj_b);
         if (e == cudaSuccess) e = cudaMalloc(&g->d_units, off_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_block_sums, g->n_blocks * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_block_sums, g->n_block_sums * sizeof(int64_t));
         if (e == cudaSuccess) e = cudaMalloc(&g->d_ctl, ctl_bytes());
         for (auto& ev : g->ev)
             if (e == cudaSuccess) e = cudaEventCreate(&ev);

@@ -203,12 +203,23 @@ std::vector<int> materialisation_order(const Pat& P, const Reduction& R) {
             int ed = pending[i];
             bool ps = placed >> P.s[ed] & 1u, pd = placed >> P.d[ed] & 1u;
             if (!ps && !pd) continue;
+            const uint32_t before = placed;
+            const size_t g0 = order.size();
             if (!ps || !pd) {
                 int x = ps ? P.d[ed] : P.s[ed];
                 order.push_back(x);
                 placed |= 1u << x;
             }
             place_covered(place_covered, ed);
+            // Vertices materialised in one step are explored smallest set
+            // first (Alg. 2 iterates the endpoint with fewer matchings): more
+            // arcs to the vertices placed before the step, then higher degree.
+            auto ties = [&](int x) { return __builtin_popcount((P.outb[x] | P.inb[x]) & before) +
+                                            __builtin_popcount(P.outb[x] & P.inb[x] & before); };
+            std::stable_sort(order.begin() + (long)g0, order.end(), [&](int a, int b) {
+                if (ties(a) != ties(b)) return ties(a) > ties(b);
+                return P.deg[a] > P.deg[b];
+            });
             pending.erase(pending.begin() + (long)i);
             progress = true;
             break;

@@ -54,12 +54,17 @@ struct xm_graph_s {
     int32_t* d_out_adj = nullptr;
     int32_t* d_in_off = nullptr;
     int32_t* d_in_adj = nullptr;
-    // scratch: per-node work-unit counts, scanned in place (n + 1 entries),
-    // block partial sums, and a small control block (counters, accumulators)
-    int32_t* d_units = nullptr;
+    // scratch of the matching pipeline (see xm_kernels.cu): first-level
+    // chunk counts and offsets, first-level candidate sets, work units, scan
+    // partials, and a small control block (counters, accumulators, plan)
+    int32_t* d_root_chunks = nullptr;  // n + 1
+    int32_t* d_chunk_cnt = nullptr;    // cmax + 1
+    int32_t* d_l1set = nullptr;        // max(m, 1)
+    int32_t* d_units = nullptr;        // n + 1
     int64_t* d_block_sums = nullptr;
     unsigned long long* d_ctl = nullptr;
-    int64_t n_blocks = 0;
+    int64_t n_block_sums = 0;
+    int64_t cmax = 0;
     // events around the last call's kernels (prep start, match start, match end)
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     bool timed = false;

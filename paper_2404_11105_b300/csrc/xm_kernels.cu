@@ -1,23 +1,30 @@
 // Device matcher for directed subgraph matching (plan execution, Alg. 2 of
 // the XMiner paper, re-designed for one B300 GPU).
 //
-// Work decomposition. Alg. 2 runs Explore() from every candidate of the
-// start vertex in parallel. Here the candidates of the first plan level
-// (the operand lists of the start node) are cut into work units of `unit`
-// positions; a persistent grid of warps takes units from a global counter
-// (guided self-scheduling), so the heavy start nodes of a power-law graph
-// are spread over many warps. Each warp runs the depth-first Explore()
-// recursion for its unit as an explicit stack of plan levels in shared
-// memory.
+// Pipeline of one count/enumerate call (all kernels on the caller's stream):
+//   1. first-level candidate sets. Alg. 2 materialises A^{p.start} and, for
+//      every start node, the endpoint set of the first explored edge. Here
+//      the first plan level's set C_1(v) = AND of v's operand lists (order
+//      bounds and degree filter applied) is built once per start node v into
+//      a global buffer, in fixed chunks of the driver list so that hub nodes
+//      are spread over many warps: k_l1_chunks (chunks per node), a scan,
+//      k_l1_count (survivors per chunk), a scan, k_l1_write (compaction).
+//   2. work units: each C_1(v) is cut into units of `unit` candidates
+//      (k_units + scan); the units of all start nodes form one index space.
+//   3. k_match: a persistent grid of warps takes units from a global counter
+//      (guided self-scheduling) and runs the depth-first Explore() recursion
+//      below the unit's first-level candidates as an explicit stack of plan
+//      levels in shared memory.
 //
-// Per level, the warp builds the candidate set (Alg. 2: A^{e.dest} =
-// A^{e.dest} cap Pi A^e) in chunks into a shared-memory window: lanes take
-// 32 consecutive ids of the shortest operand list (the driver), test each
+// Per deeper level the warp builds the candidate set (Alg. 2: A^{e.dest} =
+// A^{e.dest} cap Pi A^e) in chunks into a shared-memory window: lanes take 32
+// consecutive ids of the shortest operand list (the driver), test each
 // against the other operand lists by binary search, apply the order,
 // injectivity and degree filters, and compact the survivors with
-// __ballot_sync/__popc. A level whose whole candidate set fits in its
-// window is "complete" and can be reused by later levels in place of the
-// operand lists it already intersected (Sec. 5.2). The last level is never
+// __ballot_sync/__popc. A level whose whole candidate set is held (the
+// first level always, deeper levels when the set fits the window) is
+// "complete" and can replace, for later levels, the operand lists it already
+// intersected (Sec. 5.2 intermediate-result reuse). The last level is never
 // materialised: its candidates are counted (Sec. 5.3 count-only result
 // generation) or written out.
 #include <algorithm>
@@ -41,6 +48,8 @@ struct ListRef {
 struct LvState {
     const int32_t* drv;
     const int32_t* probe[XM_MAXOPS];
+    const int32_t* it_ptr;   // materialised candidates being iterated
+    const int32_t* set_ptr;  // the complete candidate set (when complete)
     int32_t plo[XM_MAXOPS];
     int32_t phi[XM_MAXOPS];
     int32_t drv_shared;
@@ -48,8 +57,8 @@ struct LvState {
     int32_t nprobe;
     int32_t c0, c1;        // cut driver range (order bounds applied)
     int32_t drv_pos, drv_end;
-    int32_t wcnt, wpos, it_hi;
-    int32_t complete;
+    int32_t wcnt, wpos, it_hi, it_shared;
+    int32_t set_len, set_shared, complete;
     int32_t empty;
 };
 
@@ -59,6 +68,8 @@ struct WarpSmem {
 };
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ constexpr int n_windows(int k) { return k > 3 ? k - 3 : 0; }
 
 __device__ __forceinline__ int32_t ld(const int32_t* p, int i, bool shared) {
     return shared ? p[i] : __ldg(p + i);
@@ -90,27 +101,32 @@ __device__ __forceinline__ void level_bounds(const XmLevel& L, const int32_t* m,
     for (uint32_t b = L.hi_mask; b; b &= b - 1) hi = min(hi, m[__ffs(b) - 1]);
 }
 
-// Operand lists of the first level for start node v, the driver (shortest
-// list, ties to the first operand) and its cut range. Shared by the unit
-// counter and the matcher so both see the same positions.
-__device__ __forceinline__ void first_level_driver(const XmPlanDev& P, const GraphDev& g, int32_t v, ListRef& drv,
-                                                   int& c0, int& c1) {
+// Operand lists of the first level for start node v: the driver (shortest
+// list, ties to the first operand), the other list if any (the first level
+// can only have an out- and an in-list of v), and the driver range cut by
+// the order bounds.
+__device__ __forceinline__ void first_level_lists(const XmPlanDev& P, const GraphDev& g, int32_t v, ListRef& drv,
+                                                  ListRef& other, int& nother, int& c0, int& c1) {
     const XmLevel& L = P.lv[1];
     drv = op_list(g, L.op_dir[0], v);
-    for (int i = 1; i < L.nops; i++) {
-        ListRef r = op_list(g, L.op_dir[i], v);
-        if (r.len < drv.len) drv = r;
+    nother = 0;
+    other = {nullptr, 0, 0};
+    if (L.nops > 1) {
+        ListRef r = op_list(g, L.op_dir[1], v);
+        nother = 1;
+        if (r.len < drv.len) { other = drv; drv = r; } else { other = r; }
     }
     int32_t lo = (L.lo_mask & 1u) ? v : -1;
     int32_t hi = (L.hi_mask & 1u) ? v : INT_MAX;
     c0 = 0;
     c1 = drv.len;
-    if (drv.len > 0) {
+    if (drv.len > 0 && (nother == 0 || other.len > 0)) {
         if (lo >= 0) c0 = lbound(drv.p, 0, drv.len, lo + 1, false);
         if (hi != INT_MAX) c1 = lbound(drv.p, c0, drv.len, hi, false);
     } else {
         c1 = 0;
     }
+    if (c1 < c0) c1 = c0;
 }
 
 __device__ __forceinline__ bool passes_degree(const GraphDev& g, int32_t x, int dmin_out, int dmin_in) {
@@ -123,19 +139,128 @@ __device__ __forceinline__ int ceil_log2p1(int len) {  // ceil(log2(len + 1))
     return 32 - __clz(len);
 }
 
-// Sets up level l for the partial match in ws.m[0..l-1]: operand lists
-// (or a complete earlier window in their place), driver, probes and the cut
-// of the driver by the order bounds. Returns algorithmic bytes (stats).
+// last index v in [0, n) with prefix[v] <= u (prefix is non-decreasing)
+__device__ __forceinline__ int owner_of(const int32_t* __restrict__ prefix, int n, int u) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ------------------------------------------------ first-level candidate sets
+
+__device__ __forceinline__ void plan_to_smem(XmPlanDev& P, const XmPlanDev* __restrict__ plan_g) {
+    for (int i = threadIdx.x; i < (int)(sizeof(XmPlanDev) / 4); i += blockDim.x)
+        reinterpret_cast<int32_t*>(&P)[i] = reinterpret_cast<const int32_t*>(plan_g)[i];
+    __syncthreads();
+}
+
+// Chunks of the first-level driver list per start node (0 when the node
+// fails the start vertex's degree filter or lies outside [r_lo, r_hi)).
+__global__ void k_l1_chunks(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+    __shared__ XmPlanDev P;
+    plan_to_smem(P, plan_g);
+    const GraphDev& g = ra.g;
+    const int n = g.n;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
+        int c = 0;
+        if (v < n && v >= ra.r_lo && v < ra.r_hi && passes_degree(g, v, P.lv[0].dout_min, P.lv[0].din_min)) {
+            ListRef d, o;
+            int no, c0, c1;
+            first_level_lists(P, g, v, d, o, no, c0, c1);
+            c = (c1 - c0 + L1_CHUNK - 1) / L1_CHUNK;
+        }
+        ra.root_chunks[v] = c;
+    }
+}
+
+// One warp per chunk: WRITE=false counts the chunk's survivors into
+// chunk_cnt[c]; WRITE=true writes them at the scanned offset chunk_cnt[c].
+template <bool WRITE, int MODE>
+__global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+    __shared__ XmPlanDev P;
+    plan_to_smem(P, plan_g);
+    const GraphDev& g = ra.g;
+    const int n = g.n;
+    const int lane = threadIdx.x & 31;
+    const int total = __ldg(ra.root_chunks + n);
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const bool filter_deg = P.k > 2;
+    const XmLevel& L1 = P.lv[1];
+    unsigned long long st_bytes = 0;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c <= ra.cmax; c += nwarps) {
+        if (c >= total) {
+            if (!WRITE && lane == 0) ra.chunk_cnt[c] = 0;
+            continue;
+        }
+        const int v = owner_of(ra.root_chunks, n, c);
+        const int j = c - __ldg(ra.root_chunks + v);
+        ListRef d, o;
+        int no, c0, c1;
+        first_level_lists(P, g, v, d, o, no, c0, c1);
+        int pos = c0 + j * L1_CHUNK;
+        const int end = min(c1, pos + L1_CHUNK);
+        int plo = 0;
+        int cnt = 0;
+        int32_t* out = WRITE ? ra.l1set + ra.chunk_cnt[c] : nullptr;
+        if (MODE == MODE_STATS && !WRITE && lane == 0) {
+            const int run = end - pos;
+            st_bytes += (j == 0 ? 8ull * (1 + no) : 0) + 4ull * run;
+            if (no) st_bytes += 4ull * min((long long)o.len, (long long)run * ceil_log2p1(o.len));
+            if (filter_deg) st_bytes += 8ull * run;
+        }
+        for (; pos < end; pos += 32) {
+            const int i = pos + lane;
+            const bool valid = i < end;
+            const int32_t x = valid ? __ldg(d.p + i) : INT_MAX;
+            bool ok = valid;
+            if (no) {
+                const int q = lbound(o.p, plo, o.len, x, false);
+                ok = ok && q < o.len && __ldg(o.p + q) == x;
+                plo = __shfl_sync(FULL, q, min(31, end - 1 - pos));
+            }
+            if (ok && filter_deg) ok = passes_degree(g, x, L1.dout_min, L1.din_min);
+            const unsigned mask = __ballot_sync(FULL, ok);
+            if (WRITE && ok) out[cnt + __popc(mask & ((1u << lane) - 1))] = x;
+            cnt += __popc(mask);
+        }
+        if (!WRITE && lane == 0) ra.chunk_cnt[c] = cnt;
+    }
+    if (MODE == MODE_STATS && !WRITE && lane == 0 && st_bytes) atomicAdd(ra.ctl + CTL_STATS + 0, st_bytes);
+}
+
+// Work units per start node: its first-level set cut into `unit` pieces.
+__global__ void k_units(RunArgs ra) {
+    const int n = ra.g.n;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
+        int u = 0;
+        if (v < n) {
+            const int len = ra.chunk_cnt[ra.root_chunks[v + 1]] - ra.chunk_cnt[ra.root_chunks[v]];
+            u = (len + ra.unit - 1) / ra.unit;
+        }
+        ra.units[v] = u;
+    }
+}
+
+// ----------------------------------------------------------------- k_match
+
+// Sets up level l >= 2 for the partial match in ws.m[0..l-1]: operand lists
+// (or a complete earlier set in their place), driver, probes and the cut of
+// the driver by the order bounds. Returns algorithmic bytes (stats).
 template <int MODE>
-__device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* wins,
-                                          int W, int l, int lane) {
+__device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane) {
     const XmLevel& L = P.lv[l];
     int32_t lo, hi;
     level_bounds(L, ws.m, lo, hi);
     ListRef lists[XM_MAXOPS + 1];
     int cnt = 0;
     const bool use_reuse = (L.reuse >= 1) && ws.st[L.reuse].complete;
-    if (use_reuse) lists[cnt++] = {wins + (size_t)(L.reuse - 1) * W, ws.st[L.reuse].wcnt, 1};
+    if (use_reuse) {
+        const LvState& R = ws.st[L.reuse];
+        lists[cnt++] = {R.set_ptr, R.set_len, R.set_shared};
+    }
     for (int i = 0; i < L.nops; i++) {
         if (use_reuse && ((L.reuse_ops >> i) & 1u)) continue;
         lists[cnt++] = op_list(g, L.op_dir[i], ws.m[L.op_level[i]]);
@@ -170,11 +295,13 @@ __device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g,
         S.probe_shared = psh;
         S.c0 = c0;
         S.c1 = empty ? c0 : c1;
+        S.drv_pos = c0;
+        S.drv_end = empty ? c0 : c1;
         S.empty = empty;
         S.complete = 0;
         S.wcnt = S.wpos = S.it_hi = 0;
         if (MODE == MODE_STATS) {
-            int run = empty ? 0 : c1 - c0;
+            const int run = empty ? 0 : c1 - c0;
             for (int i = 0; i < cnt; i++) {
                 if (lists[i].shared) continue;
                 bytes += 8;
@@ -188,14 +315,14 @@ __device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g,
     return bytes;
 }
 
-// Runs the driver range [pos, end) of level l through probes and filters
-// 32 ids at a time. With WINDOW the survivors are compacted into `win`
-// (stopping when fewer than 32 slots are left); otherwise they are counted
-// or emitted. cnt_a/cnt_b count survivors from driver positions < a / < b.
+// Runs the driver range [drv_pos, drv_end) of level l through probes and
+// filters 32 ids at a time. With WINDOW the survivors are compacted into
+// `win` (stopping when fewer than 32 slots are left); otherwise they are
+// counted or emitted.
 template <int MODE, bool WINDOW>
 __device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, LvState& S, int l,
-                                         int32_t* win, int W, int lane, bool filter_deg, int a, int b, int& cnt_a,
-                                         int& cnt_b, const RunArgs& ra, unsigned long long& stat_bytes) {
+                                         int32_t* win, int W, int lane, const RunArgs& ra,
+                                         unsigned long long& stat_bytes) {
     const XmLevel& L = P.lv[l];
     const bool dsh = S.drv_shared;
     const int np = S.nprobe;
@@ -224,15 +351,13 @@ __device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, 
             for (uint32_t nm = L.neq_mask; nm; nm &= nm - 1)
                 if (x == ws.m[__ffs(nm) - 1]) ok = false;
         }
-        if (ok && filter_deg) ok = passes_degree(g, x, L.dout_min, L.din_min);
+        if (WINDOW && ok) ok = passes_degree(g, x, L.dout_min, L.din_min);
         const unsigned mask = __ballot_sync(FULL, ok);
         const int rank = __popc(mask & ((1u << lane) - 1));
         if (WINDOW) {
             if (ok) win[wcnt + rank] = x;
             wcnt += __popc(mask);
-            cnt_a += __popc(__ballot_sync(FULL, ok && i < a));
-            cnt_b += __popc(__ballot_sync(FULL, ok && i < b));
-            if (MODE == MODE_STATS && lane == 0 && filter_deg) stat_bytes += 8ull * min(32, end - pos);
+            if (MODE == MODE_STATS && lane == 0) stat_bytes += 8ull * min(32, end - pos);
         } else if (MODE == MODE_EMIT) {
             const int c = __popc(mask);
             unsigned long long base = 0;
@@ -260,21 +385,15 @@ __device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, 
     return leaf;
 }
 
-// Count (or emit) the candidates of the last level l over driver positions
-// [a, b) (b = -1: the whole cut range).
+// Count (or emit) the candidates of the last level l >= 2.
 template <int MODE>
-__device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* wins, int W,
-                                         int l, int lane, int a, int b, const RunArgs& ra,
-                                         unsigned long long& stat_bytes, unsigned long long& leaf_elems) {
-    stat_bytes += setup_level<MODE>(P, g, ws, wins, W, l, lane);
+__device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane,
+                                         const RunArgs& ra, unsigned long long& stat_bytes,
+                                         unsigned long long& leaf_elems) {
+    stat_bytes += setup_level<MODE>(P, g, ws, l, lane);
     LvState& S = ws.st[l];
     if (S.empty) return 0;
-    int pos = S.c0, end = S.c1;
-    if (b >= 0) {
-        pos = max(pos, a);
-        end = min(end, b);
-    }
-    if (pos >= end) return 0;
+    const int pos = S.c0, end = S.c1;
     if (MODE == MODE_STATS && lane == 0) leaf_elems += end - pos;
     const XmLevel& L = P.lv[l];
     if (MODE != MODE_EMIT && S.nprobe == 0) {
@@ -287,14 +406,7 @@ __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, 
         }
         return lane == 0 ? c : 0;
     }
-    if (lane == 0) {
-        S.drv_pos = pos;
-        S.drv_end = end;
-    }
-    __syncwarp();
-    int ca = 0, cb = 0;
-    unsigned long long r = scan_level<MODE, false>(P, g, ws, S, l, nullptr, W, lane, false, 0, 0, ca, cb, ra,
-                                                   stat_bytes);
+    unsigned long long r = scan_level<MODE, false>(P, g, ws, S, l, nullptr, 0, lane, ra, stat_bytes);
     return lane == 0 ? r : 0;
 }
 
@@ -302,18 +414,16 @@ template <int MODE>
 __global__ void __launch_bounds__(512) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     extern __shared__ __align__(16) unsigned char smem[];
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(smem);
-    for (int i = threadIdx.x; i < (int)(sizeof(XmPlanDev) / 4); i += blockDim.x)
-        reinterpret_cast<int32_t*>(smem)[i] = reinterpret_cast<const int32_t*>(plan_g)[i];
-    __syncthreads();
+    plan_to_smem(P, plan_g);
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int k = P.k;
     const int W = ra.window;
-    const size_t warp_bytes = align16(sizeof(WarpSmem)) + (size_t)(k > 2 ? k - 2 : 0) * W * sizeof(int32_t);
+    const size_t warp_bytes = align16(sizeof(WarpSmem)) + (size_t)n_windows(k) * W * sizeof(int32_t);
     unsigned char* wbase = smem + align16(sizeof(XmPlanDev)) + (size_t)wib * warp_bytes;
     WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase);
-    int32_t* wins = reinterpret_cast<int32_t*>(wbase + align16(sizeof(WarpSmem)));
+    int32_t* wins = reinterpret_cast<int32_t*>(wbase + align16(sizeof(WarpSmem)));  // level l >= 2 at (l-2)*W
     const GraphDev& g = ra.g;
     const int n = g.n;
     const int total = ra.units[n];
@@ -336,53 +446,49 @@ __global__ void __launch_bounds__(512) k_match(const XmPlanDev* __restrict__ pla
         cnt = __shfl_sync(FULL, cnt, 0);
         if (cnt <= 0) break;
         for (int u = start; u < start + cnt; u++) {
-            if (root < 0 || u < ra.units[root] || u >= ra.units[root + 1]) {
-                // last node v with units[v] <= u
-                int lo = 0, hi = n;
-                while (hi - lo > 1) {
-                    int mid = (lo + hi) >> 1;
-                    if (__ldg(ra.units + mid) <= u) lo = mid; else hi = mid;
-                }
-                root = lo;
+            if (root < 0 || u < __ldg(ra.units + root) || u >= __ldg(ra.units + root + 1)) root = owner_of(ra.units, n, u);
+            const int chunk = u - __ldg(ra.units + root);
+            const int s0 = __ldg(ra.chunk_cnt + __ldg(ra.root_chunks + root));
+            const int s1 = __ldg(ra.chunk_cnt + __ldg(ra.root_chunks + root + 1));
+            const int32_t* base = ra.l1set + s0;
+            const int a = chunk * ra.unit;
+            const int b = min(s1 - s0, a + ra.unit);
+            if (MODE == MODE_STATS && lane == 0) {
+                st_units++;
+                st_bytes += 4ull * (b - a);
             }
-            const int chunk = u - ra.units[root];
-            if (MODE == MODE_STATS) st_units++;
-            // first level: driver positions of this unit
-            ListRef d1;
-            int c0, c1;
-            first_level_driver(P, g, root, d1, c0, c1);
-            const int a = c0 + chunk * ra.unit;
-            const int b = min(c1, a + ra.unit);
-            if (lane == 0) ws.m[0] = root;
-            __syncwarp();
-            if (MODE == MODE_STATS && chunk == 0 && lane == 0) st_bytes += 16;  // start node degree check
             if (k == 2) {
-                acc += leaf_level<MODE>(P, g, ws, wins, W, 1, lane, a, b, ra, st_bytes, st_leaf);
+                // the first level is the last: every candidate is a match
+                if (MODE == MODE_EMIT) {
+                    for (int p = a; p < b; p += 32) {
+                        const bool ok = p + lane < b;
+                        const unsigned mask = __ballot_sync(FULL, ok);
+                        unsigned long long o = 0;
+                        if (lane == 0) o = atomicAdd(ra.ctl + CTL_EMIT, (unsigned long long)__popc(mask));
+                        o = __shfl_sync(FULL, o, 0) + lane;
+                        if (ok && o < ra.capacity) {
+                            ra.out[o * 2 + P.order[0]] = root;
+                            ra.out[o * 2 + P.order[1]] = __ldg(base + p + lane);
+                        }
+                    }
+                }
+                if (lane == 0) acc += b - a;
                 continue;
             }
-            unsigned long long sb = setup_level<MODE>(P, g, ws, wins, W, 1, lane);
-            if (MODE == MODE_STATS && chunk == 0) st_bytes += sb;
-            if (MODE == MODE_STATS && lane == 0) st_sets++;
-            LvState& S1 = ws.st[1];
-            if (S1.empty) continue;
-            {
-                int ca = 0, cb = 0;
-                unsigned long long dummy = 0;
-                if (S1.c1 - S1.c0 <= W) {
-                    // whole first-level set fits: build it all (reusable), iterate the unit's part
-                    if (lane == 0) { S1.drv_pos = S1.c0; S1.drv_end = S1.c1; }
-                    __syncwarp();
-                    scan_level<MODE, true>(P, g, ws, S1, 1, wins, W, lane, true, a, b, ca, cb, ra, dummy);
-                    if (lane == 0) { S1.complete = 1; S1.wpos = ca; S1.it_hi = cb; }
-                } else {
-                    if (lane == 0) { S1.drv_pos = a; S1.drv_end = b; }
-                    __syncwarp();
-                    scan_level<MODE, true>(P, g, ws, S1, 1, wins, W, lane, true, 0, 0, ca, cb, ra, dummy);
-                    if (lane == 0) { S1.complete = 0; S1.wpos = 0; S1.it_hi = S1.wcnt; }
-                }
-                if (MODE == MODE_STATS && chunk == 0) st_bytes += dummy;
-                __syncwarp();
+            if (lane == 0) {
+                ws.m[0] = root;
+                LvState& S1 = ws.st[1];
+                S1.it_ptr = base;
+                S1.it_shared = 0;
+                S1.wpos = a;
+                S1.it_hi = b;
+                S1.set_ptr = base;
+                S1.set_len = s1 - s0;
+                S1.set_shared = 0;
+                S1.complete = 1;
+                S1.drv_pos = S1.drv_end = 0;
             }
+            __syncwarp();
             // depth-first over levels 1 .. k-2; the last level is counted
             int l = 1;
             while (l >= 1) {
@@ -391,38 +497,38 @@ __global__ void __launch_bounds__(512) k_match(const XmPlanDev* __restrict__ pla
                     if (S.complete || S.drv_pos >= S.drv_end) { l--; continue; }
                     if (lane == 0) { S.wcnt = 0; S.wpos = 0; }
                     __syncwarp();
-                    int ca = 0, cb = 0;
-                    scan_level<MODE, true>(P, g, ws, S, l, wins + (size_t)(l - 1) * W, W, lane, true, 0, 0, ca, cb,
-                                           ra, st_bytes);
+                    scan_level<MODE, true>(P, g, ws, S, l, wins + (size_t)(l - 2) * W, W, lane, ra, st_bytes);
                     if (lane == 0) S.it_hi = S.wcnt;
                     __syncwarp();
                     continue;
                 }
-                const int32_t x = wins[(size_t)(l - 1) * W + S.wpos];
+                const int32_t x = ld(S.it_ptr, S.wpos, S.it_shared);
                 __syncwarp();
                 if (lane == 0) { S.wpos++; ws.m[l] = x; }
                 __syncwarp();
                 if (MODE == MODE_STATS && lane == 0) st_ext++;
                 if (l + 1 == k - 1) {
-                    acc += leaf_level<MODE>(P, g, ws, wins, W, l + 1, lane, 0, -1, ra, st_bytes, st_leaf);
+                    acc += leaf_level<MODE>(P, g, ws, l + 1, lane, ra, st_bytes, st_leaf);
                     if (MODE == MODE_STATS && lane == 0) st_sets++;
                     continue;
                 }
                 // descend: set up level l+1 and build its first window
                 const int nl = l + 1;
-                st_bytes += setup_level<MODE>(P, g, ws, wins, W, nl, lane);
+                st_bytes += setup_level<MODE>(P, g, ws, nl, lane);
                 if (MODE == MODE_STATS && lane == 0) st_sets++;
                 LvState& N = ws.st[nl];
                 if (N.empty) continue;
-                if (lane == 0) { N.drv_pos = N.c0; N.drv_end = N.c1; }
-                __syncwarp();
-                int ca = 0, cb = 0;
-                scan_level<MODE, true>(P, g, ws, N, nl, wins + (size_t)(nl - 1) * W, W, lane, true, 0, 0, ca, cb,
-                                       ra, st_bytes);
+                int32_t* win = wins + (size_t)(nl - 2) * W;
+                scan_level<MODE, true>(P, g, ws, N, nl, win, W, lane, ra, st_bytes);
                 if (lane == 0) {
                     N.complete = N.drv_pos >= N.drv_end;
+                    N.it_ptr = win;
+                    N.it_shared = 1;
                     N.wpos = 0;
                     N.it_hi = N.wcnt;
+                    N.set_ptr = win;
+                    N.set_len = N.wcnt;
+                    N.set_shared = 1;
                 }
                 __syncwarp();
                 l = nl;
@@ -452,28 +558,10 @@ __global__ void __launch_bounds__(512) k_match(const XmPlanDev* __restrict__ pla
     }
 }
 
-// Per start node: number of work units (0 when the node fails the start
-// vertex's degree filter or lies outside [r_lo, r_hi)). units[n] = 0.
-__global__ void k_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
-    __shared__ XmPlanDev P;
-    for (int i = threadIdx.x; i < (int)(sizeof(XmPlanDev) / 4); i += blockDim.x)
-        reinterpret_cast<int32_t*>(&P)[i] = reinterpret_cast<const int32_t*>(plan_g)[i];
-    __syncthreads();
-    const GraphDev& g = ra.g;
-    const int n = g.n;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
-        int u = 0;
-        if (v < n && v >= ra.r_lo && v < ra.r_hi && passes_degree(g, v, P.lv[0].dout_min, P.lv[0].din_min)) {
-            ListRef d;
-            int c0, c1;
-            first_level_driver(P, g, v, d, c0, c1);
-            if (c1 > c0) u = (c1 - c0 + ra.unit - 1) / ra.unit;
-        }
-        ra.units[v] = u;
-    }
-}
+// ------------------------------------------------------------------- scan
+// Exclusive scan of an int32 array in place, in three passes over tiles of
+// SCAN_TILE elements (tile sums, one-block scan of the sums, tile scans).
 
-// Exclusive scan of units[0..n] in place (three passes over tiles).
 __device__ __forceinline__ long long block_sum(long long x) {
     __shared__ long long wsum[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -529,8 +617,7 @@ __device__ void block_exclusive_scan(T* vals, int per, T carry_in, T& total) {
     __syncthreads();
 }
 
-__global__ void k_scan_top(int64_t* sums, int64_t nb, int32_t* __restrict__ status) {
-    // one block: exclusive scan of the tile sums, several passes of blockDim*8
+__global__ void k_scan_top(int64_t* sums, int64_t nb, unsigned long long* __restrict__ status) {
     const int per = 8;
     long long carry = 0;
     for (int64_t base = 0; base < nb; base += (int64_t)blockDim.x * per) {
@@ -566,46 +653,54 @@ __global__ void k_scan_down(int32_t* __restrict__ v, int64_t len, const int64_t*
     }
 }
 
+cudaError_t scan_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_t stream) {
+    const int64_t nb = (len + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb > a.n_block_sums) return cudaErrorInvalidValue;
+    k_scan_reduce<<<(unsigned)nb, 1024, 0, stream>>>(v, len, a.block_sums);
+    k_scan_top<<<1, 1024, 0, stream>>>(a.block_sums, nb, a.ctl + CTL_STATUS);
+    k_scan_down<<<(unsigned)nb, 1024, 0, stream>>>(v, len, a.block_sums);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t match_smem_bytes(int k, int window, int warps) {
-    size_t warp_bytes = align16(sizeof(WarpSmem)) + (size_t)(k > 2 ? k - 2 : 0) * window * sizeof(int32_t);
+    size_t warp_bytes = align16(sizeof(WarpSmem)) + (size_t)n_windows(k) * window * sizeof(int32_t);
     return align16(sizeof(XmPlanDev)) + warp_bytes * warps;
 }
 
-static cudaError_t set_smem_attr(const void* fn, size_t bytes) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+int64_t chunk_capacity(int32_t n, int64_t m) { return (int64_t)n + (m + L1_CHUNK - 1) / L1_CHUNK; }
 
 cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev, const RunArgs& a,
-                         int warps_per_block, int blocks_per_sm, int64_t n_blocks, cudaStream_t stream,
-                         cudaEvent_t* ev) {
+                         int warps_per_block, int blocks_per_sm, cudaStream_t stream, cudaEvent_t* ev) {
     cudaError_t err;
     const int64_t len = (int64_t)a.g.n + 1;
     int dev = 0, nsm = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
     if (ev && (err = cudaEventRecord(ev[0], stream)) != cudaSuccess) return err;
-    // 1. units per start node
-    {
-        int64_t blocks = (len + 255) / 256;
-        int grid = (int)std::min<int64_t>(blocks, (int64_t)nsm * 16);
-        k_units<<<grid, 256, 0, stream>>>(plan_dev, a);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    }
-    // 2. exclusive scan in place
-    if (n_blocks < (len + SCAN_TILE - 1) / SCAN_TILE) return cudaErrorInvalidValue;
-    const int64_t nb = (len + SCAN_TILE - 1) / SCAN_TILE;
-    k_scan_reduce<<<(unsigned)nb, 1024, 0, stream>>>(a.units, len, a.block_sums);
-    k_scan_top<<<1, 1024, 0, stream>>>(a.block_sums, nb, reinterpret_cast<int32_t*>(a.ctl + CTL_STATUS));
-    k_scan_down<<<(unsigned)nb, 1024, 0, stream>>>(a.units, len, a.block_sums);
+    const int grid_nodes = (int)std::min<int64_t>((len + 255) / 256, (int64_t)nsm * 16);
+    // 1. first-level candidate sets
+    k_l1_chunks<<<grid_nodes, 256, 0, stream>>>(plan_dev, a);
+    if ((err = scan_in_place(a.root_chunks, len, a, stream)) != cudaSuccess) return err;
+    const int grid_chunks = nsm * 8;  // 256-thread blocks: 8 warps each
+    if (mode == MODE_STATS)
+        k_l1<false, MODE_STATS><<<grid_chunks, 256, 0, stream>>>(plan_dev, a);
+    else
+        k_l1<false, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, a);
+    if ((err = scan_in_place(a.chunk_cnt, (int64_t)a.cmax + 1, a, stream)) != cudaSuccess) return err;
+    k_l1<true, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, a);
+    // 2. work units
+    k_units<<<grid_nodes, 256, 0, stream>>>(a);
+    if ((err = scan_in_place(a.units, len, a, stream)) != cudaSuccess) return err;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // 3. persistent matcher
     const size_t smem = match_smem_bytes(P.k, a.window, warps_per_block);
     const void* fn = mode == MODE_STATS ? (const void*)k_match<MODE_STATS>
                      : mode == MODE_EMIT ? (const void*)k_match<MODE_EMIT>
                                          : (const void*)k_match<MODE_COUNT>;
-    if ((err = set_smem_attr(fn, smem)) != cudaSuccess) return err;
+    if ((err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return err;
     int occ = 0;
     if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps_per_block * 32, smem)) != cudaSuccess)
         return err;
