@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "matches/s"
+# kernels one xm_count enqueues: first-level chunks, count, write (each
+# followed by a 3-kernel scan except the write), units + scan, matcher
+LAUNCHES_PER_CALL = 14
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -202,6 +205,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stats", action="store_true", help="skip the instrumented run (roofline bytes)")
+    ap.add_argument("--patterns", default="", help="comma-separated subset of the workload's patterns")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -218,6 +223,10 @@ def main():
         dist.init_process_group("nccl")
 
     n, src, dst, pats, desc = workload(args.workload)
+    if args.patterns:
+        keep = args.patterns.split(",")
+        pats = {k: v for k, v in pats.items() if k in keep}
+        desc += f" (subset: {','.join(pats)})"
     g = xm.Graph(n, src, dst)
     plans = {name: xm.Plan(p) for name, p in pats.items()}
     # start-node shard of this rank (contiguous ranges balanced by arc count)
@@ -248,6 +257,7 @@ def main():
         counts = step()
 
     kernel_ms = []
+    per_pattern_ms = {name: [] for name in plans}
     step_ms = []
     if world > 1:
         dist.barrier()
@@ -261,7 +271,9 @@ def main():
             counts = {}
             for name, p in plans.items():
                 counts[name] = xm.xm_count_range(g, p, r_lo, r_hi) if world > 1 else xm.xm_count(g, p)
-                kernel_ms.append(g.last_timing()[1])
+                prep, match = g.last_timing()
+                kernel_ms.append(match)
+                per_pattern_ms[name].append(prep + match)
             ev1.record(stream)
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
@@ -283,9 +295,11 @@ def main():
     # roofline of the dominant kernel (the matcher): algorithmic bytes from an
     # instrumented, untimed run; duration from the CUDA events of the timed runs
     alg_bytes = 0
-    for name, p in plans.items():
-        c, st = xm.xm_count_stats(g, p, r_lo, r_hi)
-        alg_bytes += st["alg_bytes"]
+    if not args.no_stats:
+        for name, p in plans.items():
+            c, st = xm.xm_count_stats(g, p, r_lo, r_hi)
+            assert c == counts[name] or world > 1
+            alg_bytes += st["alg_bytes"]
     launches = len(plans) * args.steps
     avg_kernel_s = sum(kernel_ms) / len(kernel_ms) / 1000.0
     bytes_per_launch = alg_bytes / len(plans)
@@ -335,8 +349,9 @@ def main():
                        "matches_per_step": total_matches, "l2": "flushed (512 MB write) between timed steps",
                        "parallelism": f"start-node shards x{world}" if world > 1 else "1 GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 5 * launches, "clocks": clocks,
-            "counts": {k: int(v) for k, v in counts.items()}}
+            "gpu_launches": LAUNCHES_PER_CALL * launches, "clocks": clocks,
+            "counts": {k: int(v) for k, v in counts.items()},
+            "device_ms_per_pattern": {k: round(statistics.median(v), 3) for k, v in per_pattern_ms.items()}}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
