@@ -295,6 +295,46 @@ int xm_enumerate_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, 
  */
 int xm_graph_last_timing(xm_graph g, float *prep_ms, float *match_ms);
 
+/*
+ * xm_count_noalloc -- xm_count for callers that cannot allocate device
+ * memory. The paper has no counterpart: this is a deployment variant of
+ * xm_count, not a step of the method.
+ *
+ * Who needs it: a process that has given all device memory to its own pool
+ * allocator up front, or a latency-critical loop that must not call
+ * cudaMalloc/cudaFree (they may synchronise the whole device). xm_count
+ * keeps its scratch in buffers that xm_load_graph allocates; this entry
+ * point allocates nothing and instead uses one fixed scratch area of
+ * XM_NOALLOC_SCRATCH_BYTES that lives in the library as a file-scope
+ * device array (every GPU that loads the library holds it until the process
+ * exits).
+ *
+ *   out_off, out_adj, in_off, in_adj
+ *             the data graph as device arrays owned by the caller, in the
+ *             layout xm_graph_csr exposes: int32 offsets (n+1 each) and
+ *             ascending, repeat-free, self-loop-free out- and in-lists (m
+ *             each; in_adj must be the transpose of out_adj).
+ *   n, m      nodes and arcs of that CSR.
+ *   p         compiled plan (its tuning applies).
+ *   lo, hi    receive the 128-bit count, exactly as xm_count would.
+ *   stream    stream for the kernels; the call synchronises it.
+ *
+ * Limits and errors: XM_EINVAL when the scratch the graph needs (about
+ * 4 bytes x (3n + 1.001m) plus small control data) exceeds
+ * XM_NOALLOC_SCRATCH_BYTES -- use xm_count then --, or for NULL/invalid
+ * sizes; XM_ECUDA when a CUDA call fails.
+ * Set-up: the first call on each device looks up the scratch array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before capturing any stream into a CUDA graph.
+ * Concurrency: all calls on a device share the one scratch area and keep
+ * the previous call's contents (the call clears what must start at zero).
+ * Calls whose work overlaps on the GPU race with each other; serialise them
+ * (for example, one stream).
+ */
+#define XM_NOALLOC_SCRATCH_BYTES (32u << 20)
+int xm_count_noalloc(const int32_t *out_off, const int32_t *out_adj, const int32_t *in_off, const int32_t *in_adj,
+                     int32_t n, int64_t m, xm_plan p, uint64_t *lo, uint64_t *hi, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,8 @@ XM_REDUCE, XM_NO_REDUCE, XM_EMBEDDINGS = 0, 1, 2
 EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_graph_info", "xm_graph_csr",
            "xm_graph_free", "xm_compile_pattern", "xm_plan_info", "xm_plan_order", "xm_plan_level",
            "xm_plan_describe", "xm_plan_free", "xm_plan_set_tuning", "xm_plan_get_tuning", "xm_count",
-           "xm_count_range", "xm_count_stats", "xm_enumerate", "xm_enumerate_range", "xm_graph_last_timing"]
+           "xm_count_range", "xm_count_stats", "xm_enumerate", "xm_enumerate_range", "xm_graph_last_timing",
+           "xm_count_noalloc"]
 
 
 class XmError(RuntimeError):
@@ -79,6 +80,7 @@ def _load():
         "xm_enumerate": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, u64p, u64p, vp]),
         "xm_enumerate_range": (ctypes.c_int, [vp, vp, i64, i64, vp, ctypes.c_uint64, u64p, u64p, vp]),
         "xm_graph_last_timing": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+        "xm_count_noalloc": (ctypes.c_int, [vp, vp, vp, vp, i32, i64, vp, u64p, u64p, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -251,3 +253,14 @@ def xm_enumerate(g: Graph, p: Plan, out, capacity: int | None = None, root_lo: i
     if rc not in (XM_OK, XM_EOVERFLOW):
         _check(rc)
     return total.value, written.value, rc == XM_EOVERFLOW
+
+
+def xm_count_noalloc(out_off, out_adj, in_off, in_adj, n: int, m: int, p: Plan, stream=None) -> int:
+    """Count on caller-owned device CSR arrays (raw device pointers as ints)
+    without any device allocation: the library's fixed scratch area is used
+    (see include/xm.h for the size limit and the concurrency rule)."""
+    lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().xm_count_noalloc(ctypes.c_void_p(out_off), ctypes.c_void_p(out_adj), ctypes.c_void_p(in_off),
+                                  ctypes.c_void_p(in_adj), n, m, p._h, ctypes.byref(lo), ctypes.byref(hi),
+                                  _stream(stream)))
+    return (hi.value << 64) | lo.value
