@@ -328,7 +328,8 @@ def main():
             ev1.record(stream)
             ev1.synchronize()
             e2e_ms.append(ev0.elapsed_time(ev1))
-            h2d = (2 * (g2.n + 1) + 2 * g2.m) * 4 + len(plans) * 1024
+            # CSR offsets + lists, hash-index offsets, one plan copy per count
+            h2d = (2 * (g2.n + 1) + 2 * g2.m) * 4 + 2 * (g2.n + 1) * 8 + len(plans) * 1024
             g2.free()
             assert c2 == counts
         e2e = {"value": total_matches / (statistics.median(e2e_ms) / 1000.0), "unit": "matches/s",

@@ -47,6 +47,10 @@ static void free_graph(xm_graph_s* g) {
     cudaFree(g->d_out_adj);
     cudaFree(g->d_in_off);
     cudaFree(g->d_in_adj);
+    cudaFree(g->d_out_hoff);
+    cudaFree(g->d_out_htab);
+    cudaFree(g->d_in_hoff);
+    cudaFree(g->d_in_htab);
     cudaFree(g->d_root_chunks);
     cudaFree(g->d_chunk_cnt);
     cudaFree(g->d_l1set);
@@ -77,7 +81,8 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
     r_lo = std::max<int64_t>(r_lo, 0);
     r_hi = std::min<int64_t>(r_hi, g->n);
     RunArgs a;
-    a.g = {g->d_out_off, g->d_out_adj, g->d_in_off, g->d_in_adj, g->n};
+    a.g = {g->d_out_off, g->d_out_adj, g->d_in_off, g->d_in_adj, g->n,
+           g->d_out_hoff, g->d_out_htab, g->d_in_hoff, g->d_in_htab};
     a.root_chunks = g->d_root_chunks;
     a.chunk_cnt = g->d_chunk_cnt;
     a.l1set = g->d_l1set;
@@ -207,10 +212,32 @@ int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, 
         if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_in_off, H.in_off.data(), off_b, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess && am) e = cudaMemcpyAsync(g->d_out_adj, H.out_adj.data(), am, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess && am) e = cudaMemcpyAsync(g->d_in_adj, H.in_adj.data(), am, cudaMemcpyHostToDevice, stream);
+        // hash index: per-list table offsets on the host, tables built on the device
+        std::vector<int64_t> hoff_out(n + 1, 0), hoff_in(n + 1, 0);
+        for (int32_t v = 0; v < n; v++) {
+            hoff_out[v + 1] = hoff_out[v] + hash_table_size(H.out_off[v + 1] - H.out_off[v]);
+            hoff_in[v + 1] = hoff_in[v] + hash_table_size(H.in_off[v + 1] - H.in_off[v]);
+        }
+        g->hash_slots = hoff_out[n] + hoff_in[n];
+        const size_t hoff_b = ((size_t)n + 1) * sizeof(int64_t);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_out_hoff, hoff_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_in_hoff, hoff_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_out_htab, (size_t)std::max<int64_t>(hoff_out[n], 1) * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_in_htab, (size_t)std::max<int64_t>(hoff_in[n], 1) * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_out_hoff, hoff_out.data(), hoff_b, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_in_hoff, hoff_in.data(), hoff_b, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess && hoff_out[n])
+            e = cudaMemsetAsync(g->d_out_htab, 0xFF, (size_t)hoff_out[n] * sizeof(int32_t), stream);
+        if (e == cudaSuccess && hoff_in[n])
+            e = cudaMemsetAsync(g->d_in_htab, 0xFF, (size_t)hoff_in[n] * sizeof(int32_t), stream);
+        if (e == cudaSuccess) e = build_hash_index(g->d_out_off, g->d_out_adj, g->d_out_hoff, g->d_out_htab, n, stream);
+        if (e == cudaSuccess) e = build_hash_index(g->d_in_off, g->d_in_adj, g->d_in_hoff, g->d_in_htab, n, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) {
             free_graph(g);
-            return cuda_fail(e, "graph upload");
+            cudaGetLastError();
+            set_error(std::string("graph upload / index build: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA;
         }
         *out = g;
         return XM_OK;

@@ -54,6 +54,12 @@ struct xm_graph_s {
     int32_t* d_out_adj = nullptr;
     int32_t* d_in_off = nullptr;
     int32_t* d_in_adj = nullptr;
+    // hash index of the lists (see xm_index.cu)
+    int64_t* d_out_hoff = nullptr;
+    int32_t* d_out_htab = nullptr;
+    int64_t* d_in_hoff = nullptr;
+    int32_t* d_in_htab = nullptr;
+    int64_t hash_slots = 0;
     // scratch of the matching pipeline (see xm_kernels.cu): first-level
     // chunk counts and offsets, first-level candidate sets, work units, scan
     // partials, and a small control block (counters, accumulators, plan)

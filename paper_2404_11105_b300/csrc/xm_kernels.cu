@@ -43,11 +43,15 @@ struct ListRef {
     const int32_t* p;
     int32_t len;
     int32_t shared;
+    const int32_t* tab;  // hash table of the list, or null
+    uint32_t T;          // its size (0: none)
 };
 
 struct LvState {
     const int32_t* drv;
     const int32_t* probe[XM_MAXOPS];
+    const int32_t* ptab[XM_MAXOPS];  // probe hash tables (null: binary search)
+    uint32_t pT[XM_MAXOPS];
     const int32_t* it_ptr;   // materialised candidates being iterated
     const int32_t* set_ptr;  // the complete candidate set (when complete)
     int32_t plo[XM_MAXOPS];
@@ -85,12 +89,29 @@ __device__ __forceinline__ int lbound(const int32_t* p, int lo, int hi, int32_t 
 }
 
 __device__ __forceinline__ ListRef op_list(const GraphDev& g, int dir, int32_t v) {
-    if (dir == XM_DIR_OUT) {
-        int b = __ldg(g.out_off + v), e = __ldg(g.out_off + v + 1);
-        return {g.out_adj + b, e - b, 0};
+    const bool out = dir == XM_DIR_OUT;
+    const int32_t* off = out ? g.out_off : g.in_off;
+    const int b = __ldg(off + v), e = __ldg(off + v + 1);
+    ListRef r{(out ? g.out_adj : g.in_adj) + b, e - b, 0, nullptr, 0};
+    const int64_t* hoff = out ? g.out_hoff : g.in_hoff;
+    if (hoff && r.len >= HASH_MIN_LEN) {
+        const int64_t t0 = __ldg(hoff + v);
+        r.T = (uint32_t)(__ldg(hoff + v + 1) - t0);
+        r.tab = (out ? g.out_htab : g.in_htab) + t0;
     }
-    int b = __ldg(g.in_off + v), e = __ldg(g.in_off + v + 1);
-    return {g.in_adj + b, e - b, 0};
+    return r;
+}
+
+// Is x in the list whose hash table is tab[0..T)? (linear probing; a table
+// is at most half full, so the scan stops at an empty slot)
+__device__ __forceinline__ bool hash_has(const int32_t* __restrict__ tab, uint32_t T, int32_t x) {
+    uint32_t h = hash_slot(x, T);
+    for (;;) {
+        const int32_t y = __ldg(tab + h);
+        if (y == x) return true;
+        if (y < 0) return false;
+        h = (h + 1) & (T - 1);
+    }
 }
 
 // Order bounds of a level: candidates x must satisfy lo < x < hi.
@@ -110,7 +131,7 @@ __device__ __forceinline__ void first_level_lists(const XmPlanDev& P, const Grap
     const XmLevel& L = P.lv[1];
     drv = op_list(g, L.op_dir[0], v);
     nother = 0;
-    other = {nullptr, 0, 0};
+    other = {nullptr, 0, 0, nullptr, 0};
     if (L.nops > 1) {
         ListRef r = op_list(g, L.op_dir[1], v);
         nother = 1;
@@ -217,9 +238,13 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
             const int32_t x = valid ? __ldg(d.p + i) : INT_MAX;
             bool ok = valid;
             if (no) {
-                const int q = lbound(o.p, plo, o.len, x, false);
-                ok = ok && q < o.len && __ldg(o.p + q) == x;
-                plo = __shfl_sync(FULL, q, min(31, end - 1 - pos));
+                if (o.T) {
+                    ok = ok && hash_has(o.tab, o.T, x);
+                } else {
+                    const int q = lbound(o.p, plo, o.len, x, false);
+                    ok = ok && q < o.len && __ldg(o.p + q) == x;
+                    plo = __shfl_sync(FULL, q, min(31, end - 1 - pos));
+                }
             }
             if (ok && filter_deg) ok = passes_degree(g, x, L1.dout_min, L1.din_min);
             const unsigned mask = __ballot_sync(FULL, ok);
@@ -256,10 +281,17 @@ __device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g,
     level_bounds(L, ws.m, lo, hi);
     ListRef lists[XM_MAXOPS + 1];
     int cnt = 0;
-    const bool use_reuse = (L.reuse >= 1) && ws.st[L.reuse].complete;
+    bool use_reuse = (L.reuse >= 1) && ws.st[L.reuse].complete;
+    if (use_reuse && __popc(L.reuse_ops) == 1) {
+        // a reused set that equals its single operand list adds nothing but
+        // loses the list's hash index: take the list instead
+        const int i = __ffs(L.reuse_ops) - 1;
+        const ListRef r = op_list(g, L.op_dir[i], ws.m[L.op_level[i]]);
+        if (r.len == ws.st[L.reuse].set_len) use_reuse = false;
+    }
     if (use_reuse) {
         const LvState& R = ws.st[L.reuse];
-        lists[cnt++] = {R.set_ptr, R.set_len, R.set_shared};
+        lists[cnt++] = {R.set_ptr, R.set_len, R.set_shared, nullptr, 0};
     }
     for (int i = 0; i < L.nops; i++) {
         if (use_reuse && ((L.reuse_ops >> i) & 1u)) continue;
@@ -286,6 +318,8 @@ __device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g,
         for (int i = 0; i < cnt; i++) {
             if (i == d) continue;
             S.probe[np] = lists[i].p;
+            S.ptab[np] = lists[i].tab;
+            S.pT[np] = lists[i].T;
             S.plo[np] = 0;
             S.phi[np] = lists[i].len;
             if (lists[i].shared) psh |= 1 << np;
@@ -307,6 +341,7 @@ __device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g,
                 bytes += 8;
                 if (empty) continue;
                 if (i == d) bytes += 4ull * run;
+                else if (lists[i].T) bytes += 4ull * min((long long)lists[i].len, (long long)run);
                 else bytes += 4ull * min((long long)lists[i].len, (long long)run * ceil_log2p1(lists[i].len));
             }
         }
@@ -340,11 +375,16 @@ __device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, 
         bool ok = valid;
         const int last_lane = min(31, end - 1 - pos);
         for (int p = 0; p < np; p++) {
-            const bool psh = (S.probe_shared >> p) & 1;
-            const int hi = S.phi[p];
-            const int q = lbound(S.probe[p], plo[p], hi, x, psh);
-            ok = ok && q < hi && ld(S.probe[p], q, psh) == x;
-            plo[p] = __shfl_sync(FULL, q, last_lane);
+            const uint32_t T = S.pT[p];
+            if (T) {
+                if (ok) ok = hash_has(S.ptab[p], T, x);
+            } else {
+                const bool psh = (S.probe_shared >> p) & 1;
+                const int hi = S.phi[p];
+                const int q = lbound(S.probe[p], plo[p], hi, x, psh);
+                ok = ok && q < hi && ld(S.probe[p], q, psh) == x;
+                plo[p] = __shfl_sync(FULL, q, last_lane);
+            }
             if (__ballot_sync(FULL, ok) == 0) break;
         }
         if (ok) {

@@ -13,7 +13,41 @@ struct GraphDev {
     const int32_t* in_off;
     const int32_t* in_adj;
     int32_t n;
+    // optional hash index of the lists (null: binary search only): list of
+    // node v has a table of out_hoff[v+1]-out_hoff[v] slots (0 or a power of
+    // two >= 2 x its length) at out_htab + out_hoff[v]; empty slots hold -1
+    const int64_t* out_hoff = nullptr;
+    const int32_t* out_htab = nullptr;
+    const int64_t* in_hoff = nullptr;
+    const int32_t* in_htab = nullptr;
 };
+
+// Lists of at least this many ids get a hash table.
+constexpr int HASH_MIN_LEN = 32;
+
+// Multiplicative (Fibonacci) hashing, Knuth TAOCP vol. 3 sec. 6.4: the top
+// log2(T) bits of x * 2654435769 mod 2^32 select the first slot; collisions
+// probe the following slots (linear probing, wrapping).
+__host__ __device__ __forceinline__ uint32_t hash_slot(int32_t x, uint32_t T) {
+#ifdef __CUDA_ARCH__
+    const int b = __ffs((int)T) - 1;
+#else
+    const int b = __builtin_ctz(T);
+#endif
+    return ((uint32_t)x * 2654435769u) >> (32 - b);
+}
+
+// Table size for a list of `len` ids (0: no table).
+inline uint32_t hash_table_size(int64_t len) {
+    if (len < HASH_MIN_LEN) return 0;
+    uint32_t t = 1;
+    while ((int64_t)t < 2 * len) t <<= 1;
+    return t;
+}
+
+// Builds the hash tables of one CSR side on `stream` (tables pre-filled with -1).
+cudaError_t build_hash_index(const int32_t* off, const int32_t* adj, const int64_t* hoff, int32_t* htab, int32_t n,
+                             cudaStream_t stream);
 
 // Layout of the per-graph control block (unsigned long long words).
 enum {
