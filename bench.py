@@ -140,6 +140,30 @@ def profiled_traffic(workload_name):
     return None
 
 
+# ------------------------------------------------------- sharding (N > 1) --
+
+def shard_bounds(n, src, dst, world):
+    """Contiguous start-node ranges, one per rank, balanced by arc count
+    (out + in degree); together they cover [0, n) exactly once."""
+    if world <= 1:
+        return [(0, n)]
+    deg = np.bincount(src, minlength=n).astype(np.int64) + np.bincount(dst, minlength=n)
+    cum = np.cumsum(deg)
+    cuts = [0] + [int(np.searchsorted(cum, cum[-1] * r / world)) for r in range(1, world)] + [n]
+    for r in range(1, len(cuts)):
+        cuts[r] = max(cuts[r], cuts[r - 1])
+    return [(cuts[r], cuts[r + 1]) for r in range(world)]
+
+
+def allreduce_counts(counts, dist, device="cpu"):
+    """Sum exact (up to 2^93) per-pattern counts over ranks: each count is
+    split into three 31-bit limbs so int64 sums cannot overflow."""
+    t = __import__("torch").tensor([[c >> 62, (c >> 31) & 0x7FFFFFFF, c & 0x7FFFFFFF] for c in counts.values()],
+                                   dtype=__import__("torch").int64, device=device)
+    dist.all_reduce(t)
+    return {name: (a << 62) + (b << 31) + c for name, (a, b, c) in zip(counts, t.cpu().tolist())}
+
+
 # ----------------------------------------------------------- oracle (CPU) --
 
 def oracle_sample(n, src, dst, pats, budget_s, seed=0):
@@ -192,6 +216,104 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------- batch arm ----
+
+def run_batch(args):
+    """Many patterns x many small graphs: one persistent launch (CUDA graph,
+    autotuned) vs one launch per pattern vs one xm_count call per pair."""
+    import torch
+    import paper_2404_11105_b300 as xm
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    G, P = args.batch_graphs, args.batch_patterns
+    t0 = time.perf_counter()
+    graphs = [xm.Graph(*synth.small_graph(i, seed=5)) for i in range(G)]
+    pats = [synth.batch_pattern(i, seed=4) for i in range(P)]
+    plans = [xm.Plan(p) for p in pats]
+    load_s = time.perf_counter() - t0
+    pairs = [(pi, gi) for pi in range(P) for gi in range(G)]
+    npairs = len(pairs)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return out
+
+    batch = xm.Batch(plans, graphs, pairs)
+    # autotuner on a sub-batch of pairs (every 16th pair), then applied to all
+    sub = xm.Batch(plans, graphs, pairs[::16])
+    cands = [(w, u, wpb, 0, 0) for w in (128, 256) for u in (16, 64, 256) for wpb in (4, 8)]
+    best, best_ms = sub.tune(cands, reps=2)
+    sub.free()
+    batch.set_tuning(**best)
+    for _ in range(args.warmup):
+        batch.run(graph=True)
+    torch.cuda.synchronize()
+    counts = None
+
+    def one_launch():
+        nonlocal counts
+        batch.run(graph=True)
+        counts = batch.counts()
+
+    with ClockSampler(0) as clk:
+        ms_batch = timed(one_launch, args.steps)
+    clocks = clk.summary()
+    # one launch per pattern (same kernel, P launches)
+    per_pattern = [xm.Batch([plans[pi]], graphs, [(0, gi) for gi in range(G)]) for pi in range(P)]
+    for b in per_pattern:
+        b.set_tuning(**best)
+    pp_counts = []
+
+    def pattern_launches():
+        pp_counts.clear()
+        for b in per_pattern:
+            b.run()
+        for b in per_pattern:
+            pp_counts.extend(b.counts())
+
+    ms_pp = timed(pattern_launches, max(1, args.steps // 2))
+    assert pp_counts == counts, "per-pattern launches disagree with the single batched launch"
+    # one xm_count call per pair on a seeded sample, extrapolated
+    rng = np.random.default_rng(7)
+    sample = rng.choice(npairs, size=min(args.batch_single_sample, npairs), replace=False)
+
+    def singles():
+        for i in sample:
+            pi, gi = pairs[i]
+            c = xm.xm_count(graphs[gi], plans[pi])
+            assert c == counts[i]
+
+    ms_single_sample = timed(singles, 1)[0]
+    ms_single = ms_single_sample * npairs / len(sample)
+    ms = statistics.median(ms_batch)
+    total = sum(counts)
+    line = {"metric": "patterns/s", "value": npairs / (ms / 1000.0), "unit": "(pattern, graph) pairs/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{P} random connected patterns (k 3-6, density 0.3-0.7, seed 4) x {G} small "
+                                   f"graphs (n log-uniform 50-5000, mean out-degree 4-12, ER/R-MAT alternating, "
+                                   f"seed 5)", "pairs": npairs, "matches_per_step": total,
+                       "graph_load_s": round(load_s, 1), "autotuned": best,
+                       "autotune_sub_batch_ms": round(best_ms, 3)},
+            "matches_per_s": total / (ms / 1000.0),
+            "vs_one_launch_per_pattern": {"ms": statistics.median(ms_pp),
+                                          "speedup": statistics.median(ms_pp) / ms},
+            "vs_one_call_per_pair": {"ms_extrapolated": ms_single, "sample_pairs": int(len(sample)),
+                                     "speedup": ms_single / ms},
+            "gpu_launches": args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------- GPU arm ----
 
 def main():
@@ -200,7 +322,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="xm", choices=["xm", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rmat24"])
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rmat24", "batch"])
+    ap.add_argument("--batch-graphs", type=int, default=10000)
+    ap.add_argument("--batch-patterns", type=int, default=256)
+    ap.add_argument("--batch-single-sample", type=int, default=400,
+                    help="pairs timed one xm_count call at a time (extrapolated)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
@@ -210,6 +336,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
 
     import torch
     import torch.distributed as dist
@@ -229,14 +357,7 @@ def main():
         desc += f" (subset: {','.join(pats)})"
     g = xm.Graph(n, src, dst)
     plans = {name: xm.Plan(p) for name, p in pats.items()}
-    # start-node shard of this rank (contiguous ranges balanced by arc count)
-    if world > 1:
-        deg = np.bincount(src, minlength=n).astype(np.int64) + np.bincount(dst, minlength=n)
-        cum = np.cumsum(deg)
-        cuts = [0] + [int(np.searchsorted(cum, cum[-1] * r / world)) for r in range(1, world)] + [n]
-        r_lo, r_hi = cuts[rank], cuts[rank + 1]
-    else:
-        r_lo, r_hi = 0, n
+    r_lo, r_hi = shard_bounds(n, src, dst, world)[rank]
 
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -246,11 +367,7 @@ def main():
         for name, p in plans.items():
             counts[name] = xm.xm_count_range(g, p, r_lo, r_hi) if world > 1 else xm.xm_count(g, p)
         if world > 1:
-            t = torch.tensor([[c >> 62, (c >> 31) & 0x7FFFFFFF, c & 0x7FFFFFFF] for c in counts.values()],
-                             dtype=torch.int64, device="cuda")
-            dist.all_reduce(t)
-            tt = t.cpu().tolist()
-            counts = {name: (a << 62) + (b << 31) + c for name, (a, b, c) in zip(counts, tt)}
+            counts = allreduce_counts(counts, dist, device="cuda")
         return counts
 
     for _ in range(args.warmup):

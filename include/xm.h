@@ -180,8 +180,8 @@ int xm_plan_describe(xm_plan p, char *buf, int32_t cap);
 typedef struct {
     int32_t vertex;
     int32_t nops;
-    int32_t op_level[7];
-    int32_t op_dir[7];
+    int32_t op_level[14];
+    int32_t op_dir[14];
     int32_t reuse;
     uint32_t reuse_ops;
     int32_t dout_min;
@@ -205,13 +205,19 @@ void xm_plan_free(xm_plan p);
  *   unit             positions of the first level's candidate list handed
  *                    out as one work unit (1..65536);
  *   warps_per_block  1..32;
- *   blocks_per_sm    resident blocks per SM to launch (persistent grid).
+ *   blocks_per_sm    resident blocks per SM to launch (persistent grid);
+ *   budget_ms        work budget: when the matcher has run this long (GPU
+ *                    global timer) every warp stops at its next check and
+ *                    the call returns XM_ETIMEOUT with no count (0 = none).
+ *                    The kernel always finishes and the context stays
+ *                    usable.
  */
 typedef struct {
     int32_t window;
     int32_t unit;
     int32_t warps_per_block;
     int32_t blocks_per_sm;
+    int32_t budget_ms;  /* device-time budget of one call's matcher kernel, 0 = none */
 } xm_tuning;
 
 /* Sets the tuning used by later calls with this plan (copied). */
@@ -294,6 +300,70 @@ int xm_enumerate_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, 
  * Errors: XM_EINVAL (no call yet), XM_ECUDA.
  */
 int xm_graph_last_timing(xm_graph g, float *prep_ms, float *match_ms);
+
+/* ------------------------------------------------------------- batches */
+
+/*
+ * Batched matching: many independent (pattern, graph) matching problems in
+ * one persistent kernel launch. Not in the paper, which runs one pattern on
+ * one graph; each pair's count is exactly what xm_count returns for it.
+ *
+ * xm_batch_create -- describe a batch.
+ *   np, plans    compiled plans (borrowed handles; they must outlive the
+ *                batch only until this call returns: plans are copied).
+ *   ng, graphs   graph handles on the current device (must outlive the
+ *                batch: their device memory is read at every run).
+ *   npairs       number of (plan, graph) pairs, >= 1.
+ *   pair_pg      host array of 2*npairs int32: pair i matches plan
+ *                pair_pg[2i] against graph pair_pg[2i+1].
+ *   out          receives the batch handle (device descriptor, counters).
+ * Errors: XM_EINVAL for bad indices/handles, XM_ENOMEM, XM_ECUDA.
+ */
+typedef struct xm_batch_s *xm_batch;
+int xm_batch_create(int32_t np, const xm_plan *plans, int32_t ng, const xm_graph *graphs, int64_t npairs,
+                    const int32_t *pair_pg, xm_batch *out);
+
+/*
+ * Launch parameters of the batched kernel: `unit` is the number of start
+ * nodes per work unit, `window` the candidate window per level, plus warps
+ * per block and blocks per SM (0 = defaults 64, 256, 8, max resident).
+ * Synchronous (re-uploads the unit table when `unit` changes).
+ */
+int xm_batch_set_tuning(xm_batch b, const xm_tuning *t);
+int xm_batch_get_tuning(xm_batch b, xm_tuning *t);
+
+/*
+ * xm_batch_run -- enqueue one run on `stream`: zero the counters, launch the
+ * batched kernel. Does not synchronise and allocates nothing.
+ * xm_batch_run_graph -- the same work replayed from a CUDA graph captured
+ * on the first call (on a private stream); later calls only launch the
+ * graph on `stream`.
+ * xm_batch_counts -- copy the 128-bit count of every pair (2 uint64 per
+ * pair, lo then hi) into the host array out_counts; synchronises `stream`.
+ * Returns XM_ETIMEOUT (counts incomplete) when the run exceeded the batch
+ * tuning's budget_ms.
+ */
+int xm_batch_run(xm_batch b, void *stream);
+int xm_batch_run_graph(xm_batch b, void *stream);
+int xm_batch_counts(xm_batch b, uint64_t *out_counts, void *stream);
+
+/*
+ * xm_batch_tune -- autotuner: times each of the ncand candidate tunings
+ * (one warm-up run, then the fastest of `reps` event-timed runs on
+ * `stream`), keeps the fastest as the batch's tuning and reports it.
+ */
+int xm_batch_tune(xm_batch b, const xm_tuning *cand, int32_t ncand, int32_t reps, xm_tuning *best, float *best_ms,
+                  void *stream);
+
+/* Frees a batch. NULL is a no-op. */
+void xm_batch_free(xm_batch b);
+
+/*
+ * xm_count_batch -- one-shot batch: create, run, read the counts
+ * (out_counts: host, 2 uint64 per pair), free. Synchronises `stream`.
+ */
+int xm_count_batch(int32_t np, const xm_plan *plans, int32_t ng, const xm_graph *graphs, int64_t npairs,
+                   const int32_t *pair_pg, uint64_t *out_counts, void *stream);
 
 /*
  * xm_count_noalloc -- xm_count for callers that cannot allocate device

@@ -26,7 +26,8 @@ EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_gr
            "xm_graph_free", "xm_compile_pattern", "xm_plan_info", "xm_plan_order", "xm_plan_level",
            "xm_plan_describe", "xm_plan_free", "xm_plan_set_tuning", "xm_plan_get_tuning", "xm_count",
            "xm_count_range", "xm_count_stats", "xm_enumerate", "xm_enumerate_range", "xm_graph_last_timing",
-           "xm_count_noalloc"]
+           "xm_count_noalloc", "xm_batch_create", "xm_batch_set_tuning", "xm_batch_get_tuning", "xm_batch_run",
+           "xm_batch_run_graph", "xm_batch_counts", "xm_batch_tune", "xm_batch_free", "xm_count_batch"]
 
 
 class XmError(RuntimeError):
@@ -37,7 +38,7 @@ class XmError(RuntimeError):
 
 class xm_tuning(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int32), ("unit", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("budget_ms", ctypes.c_int32)]
 
 
 class xm_stats(ctypes.Structure):
@@ -46,8 +47,8 @@ class xm_stats(ctypes.Structure):
 
 
 class xm_level_info(ctypes.Structure):
-    _fields_ = [("vertex", ctypes.c_int32), ("nops", ctypes.c_int32), ("op_level", ctypes.c_int32 * 7),
-                ("op_dir", ctypes.c_int32 * 7), ("reuse", ctypes.c_int32), ("reuse_ops", ctypes.c_uint32),
+    _fields_ = [("vertex", ctypes.c_int32), ("nops", ctypes.c_int32), ("op_level", ctypes.c_int32 * 14),
+                ("op_dir", ctypes.c_int32 * 14), ("reuse", ctypes.c_int32), ("reuse_ops", ctypes.c_uint32),
                 ("dout_min", ctypes.c_int32), ("din_min", ctypes.c_int32), ("lo_mask", ctypes.c_uint32),
                 ("hi_mask", ctypes.c_uint32), ("neq_mask", ctypes.c_uint32)]
 
@@ -81,6 +82,17 @@ def _load():
         "xm_enumerate_range": (ctypes.c_int, [vp, vp, i64, i64, vp, ctypes.c_uint64, u64p, u64p, vp]),
         "xm_graph_last_timing": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
         "xm_count_noalloc": (ctypes.c_int, [vp, vp, vp, vp, i32, i64, vp, u64p, u64p, vp]),
+        "xm_batch_create": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64, i32p,
+                                           ctypes.POINTER(vp)]),
+        "xm_batch_set_tuning": (ctypes.c_int, [vp, ctypes.POINTER(xm_tuning)]),
+        "xm_batch_get_tuning": (ctypes.c_int, [vp, ctypes.POINTER(xm_tuning)]),
+        "xm_batch_run": (ctypes.c_int, [vp, vp]),
+        "xm_batch_run_graph": (ctypes.c_int, [vp, vp]),
+        "xm_batch_counts": (ctypes.c_int, [vp, u64p, vp]),
+        "xm_batch_tune": (ctypes.c_int, [vp, ctypes.POINTER(xm_tuning), i32, i32, ctypes.POINTER(xm_tuning),
+                                         ctypes.POINTER(ctypes.c_float), vp]),
+        "xm_batch_free": (None, [vp]),
+        "xm_count_batch": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64, i32p, u64p, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -198,8 +210,8 @@ class Plan:
         lib().xm_plan_describe(self._h, buf, need + 1)
         return buf.value.decode()
 
-    def set_tuning(self, window=0, unit=0, warps_per_block=0, blocks_per_sm=0):
-        t = xm_tuning(window, unit, warps_per_block, blocks_per_sm)
+    def set_tuning(self, window=0, unit=0, warps_per_block=0, blocks_per_sm=0, budget_ms=0):
+        t = xm_tuning(window, unit, warps_per_block, blocks_per_sm, budget_ms)
         _check(lib().xm_plan_set_tuning(self._h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
@@ -264,3 +276,66 @@ def xm_count_noalloc(out_off, out_adj, in_off, in_adj, n: int, m: int, p: Plan, 
                                   ctypes.c_void_p(in_adj), n, m, p._h, ctypes.byref(lo), ctypes.byref(hi),
                                   _stream(stream)))
     return (hi.value << 64) | lo.value
+
+
+class Batch:
+    """Many (plan, graph) pairs matched in one persistent launch."""
+
+    def __init__(self, plans, graphs, pairs):
+        self._plans, self._graphs = list(plans), list(graphs)
+        pa = (ctypes.c_void_p * len(self._plans))(*[p._h.value for p in self._plans])
+        ga = (ctypes.c_void_p * len(self._graphs))(*[g._h.value for g in self._graphs])
+        pp = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        self.npairs = pp.shape[0]
+        h = ctypes.c_void_p()
+        _check(lib().xm_batch_create(len(self._plans), pa, len(self._graphs), ga, self.npairs,
+                                     pp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(h)))
+        self._h = h
+
+    def set_tuning(self, window=0, unit=0, warps_per_block=0, blocks_per_sm=0, budget_ms=0):
+        t = xm_tuning(window, unit, warps_per_block, blocks_per_sm, budget_ms)
+        _check(lib().xm_batch_set_tuning(self._h, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        t = xm_tuning()
+        _check(lib().xm_batch_get_tuning(self._h, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in xm_tuning._fields_}
+
+    def run(self, stream=None, graph=False):
+        fn = lib().xm_batch_run_graph if graph else lib().xm_batch_run
+        _check(fn(self._h, _stream(stream)))
+
+    def counts(self, stream=None):
+        out = np.zeros(2 * self.npairs, np.uint64)
+        _check(lib().xm_batch_counts(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _stream(stream)))
+        lo, hi = out[0::2], out[1::2]
+        return [(int(h) << 64) | int(l) for l, h in zip(lo, hi)]
+
+    def tune(self, candidates, reps=2, stream=None):
+        arr = (xm_tuning * len(candidates))(*[xm_tuning(*c) for c in candidates])
+        best = xm_tuning()
+        ms = ctypes.c_float()
+        _check(lib().xm_batch_tune(self._h, arr, len(candidates), reps, ctypes.byref(best), ctypes.byref(ms),
+                                   _stream(stream)))
+        return {f: getattr(best, f) for f, _ in xm_tuning._fields_}, ms.value
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().xm_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def xm_count_batch(plans, graphs, pairs, stream=None):
+    """One-shot batch: exact count of every (plan index, graph index) pair."""
+    b = Batch(plans, graphs, pairs)
+    try:
+        b.run(stream)
+        return b.counts(stream)
+    finally:
+        b.free()

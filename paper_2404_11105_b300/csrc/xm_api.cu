@@ -29,7 +29,7 @@ static int cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-static const xm_tuning kDefaultTuning = {512, 32, 8, 0};
+static const xm_tuning kDefaultTuning = {512, 32, 8, 0, 0};
 
 static bool is_device_ptr(const void* p) {
     if (!p) return false;
@@ -97,6 +97,7 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
     a.window = t.window;
     a.out = out;
     a.capacity = capacity;
+    a.budget_ns = (unsigned long long)t.budget_ms * 1000000ull;
     XM_CUDA(cudaMemsetAsync(g->d_ctl, 0, CTL_WORDS * sizeof(unsigned long long), stream), "cudaMemsetAsync");
     XM_CUDA(cudaMemcpyAsync(ctl_plan(g), &P.dev, sizeof(XmPlanDev), cudaMemcpyHostToDevice, stream),
             "plan upload");
@@ -106,6 +107,7 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
     unsigned long long ctl[CTL_WORDS];
     XM_CUDA(cudaMemcpyAsync(ctl, g->d_ctl, sizeof ctl, cudaMemcpyDeviceToHost, stream), "result readback");
     XM_CUDA(cudaStreamSynchronize(stream), "matcher execution");
+    if (ctl[CTL_STATUS] & STATUS_TIMEOUT) { set_error("time budget of the matcher exceeded; no count"); return XM_ETIMEOUT; }
     if (ctl[CTL_STATUS]) { set_error("work-unit count exceeds 2^31-1 (raise the unit size)"); return XM_EINVAL; }
     if (mode == MODE_EMIT) {
         *lo = ctl[CTL_EMIT];
@@ -357,6 +359,7 @@ int xm_plan_set_tuning(xm_plan p, const xm_tuning* t) {
     if (v.unit < 1 || v.unit > 65536) { set_error("unit must be in [1, 65536]"); return XM_EINVAL; }
     if (v.warps_per_block < 1 || v.warps_per_block > 16) { set_error("warps_per_block must be in [1, 16]"); return XM_EINVAL; }
     if (v.blocks_per_sm < 0 || v.blocks_per_sm > 64) { set_error("blocks_per_sm must be in [0, 64]"); return XM_EINVAL; }
+    if (v.budget_ms < 0) { set_error("budget_ms must be >= 0"); return XM_EINVAL; }
     p->tuning = v;
     return XM_OK;
 }

@@ -337,6 +337,7 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
         L.dout_min = P.dout[v];
         L.din_min = P.din[v];
         uint32_t adj_levels = 0;
+        static_assert(XM_MAXOPS >= 2 * (XM_MAXK - 1), "operand arrays too small");
         for (int j = 0; j < l; j++) {
             int u = order[j];
             if (P.arc(u, v)) { L.op_level[L.nops] = j; L.op_dir[L.nops] = XM_DIR_OUT; L.nops++; adj_levels |= 1u << j; }

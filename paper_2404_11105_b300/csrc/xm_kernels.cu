@@ -39,6 +39,44 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Work budget of a launch: the first warp to start records the start time
+// in ctl[CTL_T0]; a warp whose check finds the budget spent raises the
+// timeout status bit, and every warp stops at its next check.
+struct Budget {
+    unsigned long long deadline = 0;  // 0: unlimited
+    unsigned long long* ctl = nullptr;
+    __device__ void start(unsigned long long* c, unsigned long long budget_ns, int lane) {
+        ctl = c;
+        if (!budget_ns) return;
+        unsigned long long t0 = 0;
+        if (lane == 0) {
+            const unsigned long long now = global_ns();
+            const unsigned long long prev = atomicCAS(c + CTL_T0, 0ull, now);
+            t0 = prev ? prev : now;
+        }
+        deadline = __shfl_sync(FULL, t0, 0) + budget_ns;
+    }
+    // true when the launch must stop (warp-uniform)
+    __device__ bool expired(int lane) const {
+        if (!deadline) return false;
+        int stop = 0;
+        if (lane == 0) {
+            stop = (*((volatile unsigned long long*)(ctl + CTL_STATUS)) & STATUS_TIMEOUT) != 0;
+            if (!stop && global_ns() > deadline) {
+                atomicOr(ctl + CTL_STATUS, (unsigned long long)STATUS_TIMEOUT);
+                stop = 1;
+            }
+        }
+        return __shfl_sync(FULL, stop, 0) != 0;
+    }
+};
+
 struct ListRef {
     const int32_t* p;
     int32_t len;
@@ -71,9 +109,16 @@ struct WarpSmem {
     int32_t m[XM_MAXK];
 };
 
+__host__ __device__ size_t batch_warp_bytes_impl(int kmax, int window) {
+    return ((sizeof(XmPlanDev) + 15) & ~size_t(15)) + ((sizeof(WarpSmem) + 15) & ~size_t(15)) +
+           (size_t)(kmax > 2 ? kmax - 2 : 0) * window * sizeof(int32_t);
+}
+
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 __host__ __device__ constexpr int n_windows(int k) { return k > 3 ? k - 3 : 0; }
+
+
 
 __device__ __forceinline__ int32_t ld(const int32_t* p, int i, bool shared) {
     return shared ? p[i] : __ldg(p + i);
@@ -450,8 +495,112 @@ __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, 
     return lane == 0 ? r : 0;
 }
 
+struct Stats {
+    unsigned long long bytes = 0, ext = 0, sets = 0, units = 0, leaf = 0;
+};
+
+// Sets up level nl and builds its first window `win`; false when empty.
 template <int MODE>
-__global__ void __launch_bounds__(512) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+__device__ bool descend(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* win, int W, int nl, int lane,
+                        const RunArgs& ra, Stats& st) {
+    st.bytes += setup_level<MODE>(P, g, ws, nl, lane);
+    if (MODE == MODE_STATS && lane == 0) st.sets++;
+    LvState& N = ws.st[nl];
+    if (N.empty) return false;
+    scan_level<MODE, true>(P, g, ws, N, nl, win, W, lane, ra, st.bytes);
+    if (lane == 0) {
+        N.complete = N.drv_pos >= N.drv_end;
+        N.it_ptr = win;
+        N.it_shared = 1;
+        N.wpos = 0;
+        N.it_hi = N.wcnt;
+        N.set_ptr = win;
+        N.set_len = N.wcnt;
+        N.set_shared = 1;
+    }
+    __syncwarp();
+    return true;
+}
+
+// Depth-first extension below the first level (Alg. 2 Explore): level 1's
+// iteration state is set; levels wl0.. use windows wins + (l - wl0) * W;
+// the last level is counted (or emitted) into acc.
+template <int MODE>
+__device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* wins, int W, int wl0, int lane,
+                        const RunArgs& ra, unsigned long long& acc, Stats& st, const Budget& budget) {
+    const int k = P.k;
+    int l = 1;
+    unsigned steps = 0;
+    while (l >= 1) {
+        if ((++steps & 255u) == 0 && budget.expired(lane)) return false;
+        LvState& S = ws.st[l];
+        if (S.wpos >= S.it_hi) {
+            if (S.complete || S.drv_pos >= S.drv_end) { l--; continue; }
+            if (lane == 0) { S.wcnt = 0; S.wpos = 0; }
+            __syncwarp();
+            scan_level<MODE, true>(P, g, ws, S, l, wins + (size_t)(l - wl0) * W, W, lane, ra, st.bytes);
+            if (lane == 0) S.it_hi = S.wcnt;
+            __syncwarp();
+            continue;
+        }
+        const int32_t x = ld(S.it_ptr, S.wpos, S.it_shared);
+        __syncwarp();
+        if (lane == 0) { S.wpos++; ws.m[l] = x; }
+        __syncwarp();
+        if (MODE == MODE_STATS && lane == 0) st.ext++;
+        if (l + 1 == k - 1) {
+            acc += leaf_level<MODE>(P, g, ws, l + 1, lane, ra, st.bytes, st.leaf);
+            if (MODE == MODE_STATS && lane == 0) st.sets++;
+            continue;
+        }
+        if (descend<MODE>(P, g, ws, wins + (size_t)(l + 1 - wl0) * W, W, l + 1, lane, ra, st)) l++;
+    }
+    return true;
+}
+
+// 128-bit warp reduction of per-lane counts, added to counter[0..1].
+__device__ __forceinline__ void flush_count(unsigned long long acc, unsigned long long* counter, int lane) {
+    unsigned long long lo = acc, hi = 0;
+    for (int off = 16; off; off >>= 1) {
+        unsigned long long olo = __shfl_down_sync(FULL, lo, off);
+        unsigned long long ohi = __shfl_down_sync(FULL, hi, off);
+        unsigned long long s = lo + olo;
+        hi += ohi + (s < lo ? 1 : 0);
+        lo = s;
+    }
+    if (lane == 0 && (lo | hi)) {
+        unsigned long long old = atomicAdd(counter, lo);
+        unsigned long long carry = (old + lo < old) ? 1 : 0;
+        if (hi + carry) atomicAdd(counter + 1, hi + carry);
+    }
+}
+
+// Guided self-scheduling: lane 0 takes a batch of units proportional to
+// what is left; returns [start, start + cnt) on every lane (cnt <= 0: done,
+// or the budget is spent).
+__device__ __forceinline__ void grab_units(unsigned long long* head, long long total, int nwarps, int lane,
+                                           long long& start, int& cnt, const Budget& budget) {
+    if (budget.expired(lane)) {
+        start = total;
+        cnt = 0;
+        return;
+    }
+    long long s0 = 0;
+    int c = 0;
+    if (lane == 0) {
+        unsigned long long seen = *((volatile unsigned long long*)head);
+        long long left = total - (long long)seen;
+        int batch = left > 0 ? (int)min(64ll, max(1ll, left / (8ll * nwarps))) : 1;
+        unsigned long long s = atomicAdd(head, (unsigned long long)batch);
+        s0 = (long long)s >= total ? total : (long long)s;
+        c = (int)min((long long)batch, total - s0);
+    }
+    start = __shfl_sync(FULL, s0, 0);
+    cnt = __shfl_sync(FULL, c, 0);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     extern __shared__ __align__(16) unsigned char smem[];
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(smem);
     plan_to_smem(P, plan_g);
@@ -469,23 +618,17 @@ __global__ void __launch_bounds__(512) k_match(const XmPlanDev* __restrict__ pla
     const int total = ra.units[n];
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
 
-    unsigned long long acc = 0, st_bytes = 0, st_ext = 0, st_sets = 0, st_units = 0, st_leaf = 0;
+    unsigned long long acc = 0;
+    Stats st;
+    Budget budget;
+    budget.start(ra.ctl, ra.budget_ns, lane);
     int root = -1;
     for (;;) {
-        // guided self-scheduling: take a batch proportional to what is left
-        int start = 0, cnt = 0;
-        if (lane == 0) {
-            unsigned long long seen = *((volatile unsigned long long*)(ra.ctl + CTL_HEAD));
-            long long left = (long long)total - (long long)seen;
-            int batch = left > 0 ? (int)min(64ll, max(1ll, left / (8ll * nwarps))) : 1;
-            unsigned long long s = atomicAdd(ra.ctl + CTL_HEAD, (unsigned long long)batch);
-            start = s >= (unsigned long long)total ? total : (int)s;
-            cnt = min(batch, total - start);
-        }
-        start = __shfl_sync(FULL, start, 0);
-        cnt = __shfl_sync(FULL, cnt, 0);
+        long long start;
+        int cnt;
+        grab_units(ra.ctl + CTL_HEAD, total, nwarps, lane, start, cnt, budget);
         if (cnt <= 0) break;
-        for (int u = start; u < start + cnt; u++) {
+        for (int u = (int)start; u < (int)start + cnt; u++) {
             if (root < 0 || u < __ldg(ra.units + root) || u >= __ldg(ra.units + root + 1)) root = owner_of(ra.units, n, u);
             const int chunk = u - __ldg(ra.units + root);
             const int s0 = __ldg(ra.chunk_cnt + __ldg(ra.root_chunks + root));
@@ -494,8 +637,8 @@ __global__ void __launch_bounds__(512) k_match(const XmPlanDev* __restrict__ pla
             const int a = chunk * ra.unit;
             const int b = min(s1 - s0, a + ra.unit);
             if (MODE == MODE_STATS && lane == 0) {
-                st_units++;
-                st_bytes += 4ull * (b - a);
+                st.units++;
+                st.bytes += 4ull * (b - a);
             }
             if (k == 2) {
                 // the first level is the last: every candidate is a match
@@ -529,73 +672,90 @@ __global__ void __launch_bounds__(512) k_match(const XmPlanDev* __restrict__ pla
                 S1.drv_pos = S1.drv_end = 0;
             }
             __syncwarp();
-            // depth-first over levels 1 .. k-2; the last level is counted
-            int l = 1;
-            while (l >= 1) {
-                LvState& S = ws.st[l];
-                if (S.wpos >= S.it_hi) {
-                    if (S.complete || S.drv_pos >= S.drv_end) { l--; continue; }
-                    if (lane == 0) { S.wcnt = 0; S.wpos = 0; }
-                    __syncwarp();
-                    scan_level<MODE, true>(P, g, ws, S, l, wins + (size_t)(l - 2) * W, W, lane, ra, st_bytes);
-                    if (lane == 0) S.it_hi = S.wcnt;
-                    __syncwarp();
-                    continue;
-                }
-                const int32_t x = ld(S.it_ptr, S.wpos, S.it_shared);
-                __syncwarp();
-                if (lane == 0) { S.wpos++; ws.m[l] = x; }
-                __syncwarp();
-                if (MODE == MODE_STATS && lane == 0) st_ext++;
-                if (l + 1 == k - 1) {
-                    acc += leaf_level<MODE>(P, g, ws, l + 1, lane, ra, st_bytes, st_leaf);
-                    if (MODE == MODE_STATS && lane == 0) st_sets++;
-                    continue;
-                }
-                // descend: set up level l+1 and build its first window
-                const int nl = l + 1;
-                st_bytes += setup_level<MODE>(P, g, ws, nl, lane);
-                if (MODE == MODE_STATS && lane == 0) st_sets++;
-                LvState& N = ws.st[nl];
-                if (N.empty) continue;
-                int32_t* win = wins + (size_t)(nl - 2) * W;
-                scan_level<MODE, true>(P, g, ws, N, nl, win, W, lane, ra, st_bytes);
-                if (lane == 0) {
-                    N.complete = N.drv_pos >= N.drv_end;
-                    N.it_ptr = win;
-                    N.it_shared = 1;
-                    N.wpos = 0;
-                    N.it_hi = N.wcnt;
-                    N.set_ptr = win;
-                    N.set_len = N.wcnt;
-                    N.set_shared = 1;
-                }
-                __syncwarp();
-                l = nl;
-            }
+            if (!explore<MODE>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget)) break;
         }
     }
-    // 128-bit accumulation of the warp's count
-    unsigned long long lo = acc, hi = 0;
-    for (int off = 16; off; off >>= 1) {
-        unsigned long long olo = __shfl_down_sync(FULL, lo, off);
-        unsigned long long ohi = __shfl_down_sync(FULL, hi, off);
-        unsigned long long s = lo + olo;
-        hi += ohi + (s < lo ? 1 : 0);
-        lo = s;
-    }
-    if (lane == 0 && (lo | hi)) {
-        unsigned long long old = atomicAdd(ra.ctl + CTL_COUNT_LO, lo);
-        unsigned long long carry = (old + lo < old) ? 1 : 0;
-        if (hi + carry) atomicAdd(ra.ctl + CTL_COUNT_HI, hi + carry);
-    }
+    flush_count(acc, ra.ctl + CTL_COUNT_LO, lane);
     if (MODE == MODE_STATS && lane == 0) {
-        atomicAdd(ra.ctl + CTL_STATS + 0, st_bytes);
-        atomicAdd(ra.ctl + CTL_STATS + 1, st_ext);
-        atomicAdd(ra.ctl + CTL_STATS + 2, st_sets);
-        atomicAdd(ra.ctl + CTL_STATS + 3, st_units);
-        atomicAdd(ra.ctl + CTL_STATS + 4, st_leaf);
+        atomicAdd(ra.ctl + CTL_STATS + 0, st.bytes);
+        atomicAdd(ra.ctl + CTL_STATS + 1, st.ext);
+        atomicAdd(ra.ctl + CTL_STATS + 2, st.sets);
+        atomicAdd(ra.ctl + CTL_STATS + 3, st.units);
+        atomicAdd(ra.ctl + CTL_STATS + 4, st.leaf);
     }
+}
+
+// Batched matcher: many (plan, graph) pairs in one persistent launch. A
+// work unit is a block of `root_block` consecutive start nodes of one pair;
+// each warp keeps its own copy of the current pair's plan. The first level
+// is built per start node in a shared-memory window (the graphs are small),
+// then the same Explore() recursion runs; counts go to the pair's counter.
+__global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int W = b.window;
+    const size_t warp_bytes = batch_warp_bytes_impl(b.kmax, W);
+    unsigned char* wbase = smem + (size_t)wib * warp_bytes;
+    XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(wbase);
+    WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase + align16(sizeof(XmPlanDev)));
+    int32_t* wins = reinterpret_cast<int32_t*>(wbase + align16(sizeof(XmPlanDev)) + align16(sizeof(WarpSmem)));
+    const long long total = __ldg(b.unit_prefix + b.npairs);
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    RunArgs ra{};  // count mode: no emission buffer
+    ra.window = W;
+    GraphDev g{};
+    Stats st;
+    Budget budget;
+    budget.start(b.ctl, b.budget_ns, lane);
+    int cur = -1;
+    unsigned long long acc = 0;
+    bool stop = false;
+    for (; !stop;) {
+        long long start;
+        int cnt;
+        grab_units(b.ctl + CTL_HEAD, total, nwarps, lane, start, cnt, budget);
+        if (cnt <= 0) break;
+        for (long long u = start; u < start + cnt; u++) {
+            // pair owning unit u: last p with unit_prefix[p] <= u
+            int lo = 0, hi = b.npairs;
+            if (cur >= 0 && u >= __ldg(b.unit_prefix + cur) && u < __ldg(b.unit_prefix + cur + 1)) {
+                lo = cur;
+            } else {
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (__ldg(b.unit_prefix + mid) <= u) lo = mid; else hi = mid;
+                }
+            }
+            if (lo != cur) {
+                if (cur >= 0) flush_count(acc, b.counts + 2 * (size_t)cur, lane);
+                acc = 0;
+                cur = lo;
+                const int2 pg = b.pairs[cur];
+                __syncwarp();
+                for (int i = lane; i < (int)(sizeof(XmPlanDev) / 4); i += 32)
+                    reinterpret_cast<int32_t*>(&P)[i] = reinterpret_cast<const int32_t*>(b.plans + pg.x)[i];
+                g = b.graphs[pg.y];
+                __syncwarp();
+            }
+            const int r0 = (int)(u - __ldg(b.unit_prefix + cur)) * b.root_block;
+            const int r1 = min(r0 + b.root_block, g.n);
+            const int k = P.k;
+            for (int v = r0; v < r1; v++) {
+                if (!passes_degree(g, v, P.lv[0].dout_min, P.lv[0].din_min)) continue;
+                if (lane == 0) ws.m[0] = v;
+                __syncwarp();
+                if (k == 2) {
+                    acc += leaf_level<MODE_COUNT>(P, g, ws, 1, lane, ra, st.bytes, st.leaf);
+                    continue;
+                }
+                if (!descend<MODE_COUNT>(P, g, ws, wins, W, 1, lane, ra, st)) continue;
+                if (!explore<MODE_COUNT>(P, g, ws, wins, W, 1, lane, ra, acc, st, budget)) { stop = true; break; }
+            }
+            if (stop) break;
+        }
+    }
+    if (cur >= 0) flush_count(acc, b.counts + 2 * (size_t)cur, lane);
 }
 
 // ------------------------------------------------------------------- scan
@@ -674,7 +834,7 @@ __global__ void k_scan_top(int64_t* sums, int64_t nb, unsigned long long* __rest
         }
         carry += tot;
     }
-    if (threadIdx.x == 0 && carry > INT_MAX) *status = 1;
+    if (threadIdx.x == 0 && carry > INT_MAX) atomicOr(status, (unsigned long long)STATUS_OVERFLOW);
 }
 
 __global__ void k_scan_down(int32_t* __restrict__ v, int64_t len, const int64_t* __restrict__ sums) {
@@ -704,12 +864,33 @@ cudaError_t scan_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_
 
 }  // namespace
 
+size_t batch_warp_bytes(int kmax, int window) { return batch_warp_bytes_impl(kmax, window); }
+
 size_t match_smem_bytes(int k, int window, int warps) {
     size_t warp_bytes = align16(sizeof(WarpSmem)) + (size_t)n_windows(k) * window * sizeof(int32_t);
     return align16(sizeof(XmPlanDev)) + warp_bytes * warps;
 }
 
 int64_t chunk_capacity(int32_t n, int64_t m) { return (int64_t)n + (m + L1_CHUNK - 1) / L1_CHUNK; }
+
+cudaError_t launch_batch(const BatchDev& b, int warps_per_block, int blocks_per_sm, cudaStream_t stream) {
+    cudaError_t err;
+    int dev = 0, nsm = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    const size_t smem = batch_warp_bytes_impl(b.kmax, b.window) * warps_per_block;
+    if ((err = cudaFuncSetAttribute((const void*)k_match_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess)
+        return err;
+    int occ = 0;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_match_batch, warps_per_block * 32,
+                                                             smem)) != cudaSuccess)
+        return err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, occ) : occ;
+    k_match_batch<<<nsm * bps, warps_per_block * 32, smem, stream>>>(b);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev, const RunArgs& a,
                          int warps_per_block, int blocks_per_sm, cudaStream_t stream, cudaEvent_t* ev) {

@@ -55,7 +55,8 @@ enum {
     CTL_COUNT_LO = 1,  // 128-bit match count
     CTL_COUNT_HI = 2,
     CTL_EMIT = 3,      // enumeration cursor
-    CTL_STATUS = 4,    // error bits
+    CTL_STATUS = 4,    // error bits (1: unit count overflow, 2: time budget exceeded)
+    CTL_T0 = 5,        // global-timer start of the matcher (budget reference)
     CTL_STATS = 8,     // 8 stats words (xm_stats order)
     CTL_WORDS = 16
 };
@@ -73,11 +74,34 @@ struct RunArgs {
     int32_t r_lo, r_hi;         // start-node range
     int32_t unit;               // first-level candidates per work unit
     int32_t window;             // candidate window per deeper level (ids)
+    unsigned long long budget_ns;  // matcher time budget (0: none)
     int32_t* out;               // enumeration buffer (k ints per match)
     unsigned long long capacity;
 };
 
 enum { MODE_COUNT = 0, MODE_STATS = 1, MODE_EMIT = 2 };
+enum { STATUS_OVERFLOW = 1, STATUS_TIMEOUT = 2 };
+
+// Descriptor of a batched launch (device pointers).
+struct BatchDev {
+    const GraphDev* graphs;          // ng graphs
+    const XmPlanDev* plans;          // np plans
+    const int2* pairs;               // npairs (plan index, graph index)
+    const long long* unit_prefix;    // npairs + 1: scanned units (root blocks) per pair
+    unsigned long long* counts;      // 2 per pair (128-bit count)
+    unsigned long long* ctl;         // control block (unit counter)
+    int32_t npairs;
+    int32_t root_block;              // start nodes per work unit
+    int32_t window;                  // candidate window per level (ids)
+    unsigned long long budget_ns;    // time budget (0: none)
+    int32_t kmax;                    // largest pattern in the batch
+};
+
+// Shared memory per warp of the batched matcher.
+size_t batch_warp_bytes(int kmax, int window);
+
+// Enqueues the batched matcher (counts and control block must be zeroed).
+cudaError_t launch_batch(const BatchDev& b, int warps_per_block, int blocks_per_sm, cudaStream_t stream);
 
 // Tile of the in-place scans (elements per block).
 constexpr int SCAN_TILE = 4096;

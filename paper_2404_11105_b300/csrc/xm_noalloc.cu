@@ -103,6 +103,7 @@ extern "C" int xm_count_noalloc(const int32_t* out_off, const int32_t* out_adj, 
     a.window = p->tuning.window;
     a.out = nullptr;
     a.capacity = 0;
+    a.budget_ns = (unsigned long long)p->tuning.budget_ms * 1000000ull;
     // the control block (work counter, count accumulators, status) must
     // start at zero; every other array is fully written before it is read
     cudaError_t e = cudaMemsetAsync(a.ctl, 0, CTL_WORDS * sizeof(unsigned long long), stream);
@@ -117,6 +118,10 @@ extern "C" int xm_count_noalloc(const int32_t* out_off, const int32_t* out_adj, 
     if (e != cudaSuccess) {
         set_error(std::string("xm_count_noalloc: ") + cudaGetErrorString(e));
         return XM_ECUDA;
+    }
+    if (ctl[CTL_STATUS] & STATUS_TIMEOUT) {
+        set_error("time budget of the matcher exceeded; no count");
+        return XM_ETIMEOUT;
     }
     if (ctl[CTL_STATUS]) {
         set_error("work-unit count exceeds 2^31-1 (raise the unit size)");

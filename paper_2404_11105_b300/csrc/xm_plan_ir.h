@@ -25,7 +25,7 @@
 #include <stdint.h>
 
 #define XM_MAXK 8
-#define XM_MAXOPS 7
+#define XM_MAXOPS 14  // an out- and an in-list from each of up to 7 earlier levels
 
 enum { XM_DIR_OUT = 0, XM_DIR_IN = 1 };
 

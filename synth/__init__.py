@@ -151,3 +151,43 @@ def rmat24():
 
 TINY_PATTERNS = {"cycle3": CYCLE3, "ffl": FFL, "bifan": BIFAN}
 S24_PATTERNS = {"cycle4": CYCLE4, "bifan": BIFAN, "biparallel": BIPARALLEL, "ffchain5": FFCHAIN5}
+
+
+# ------------------------------------------------------ batch / serve recipes
+
+def rmat_graph_arcs(scale: int, n_arcs: int, seed: int, n_keep: int | None = None):
+    """R-MAT with an explicit number of drawn arcs (default a, b, c)."""
+    src = np.empty(n_arcs, np.int32)
+    dst = np.empty(n_arcs, np.int32)
+    if _L().synth_rmat(scale, n_arcs, RMAT_ABC[0], RMAT_ABC[1], RMAT_ABC[2], seed, src, dst) != 0:
+        raise ValueError("synth_rmat failed")
+    n = 1 << scale
+    if n_keep is not None and n_keep < n:
+        kept = _L().synth_trim(n_arcs, n_keep, src, dst)
+        src, dst, n = src[:kept].copy(), dst[:kept].copy(), n_keep
+    return n, src, dst
+
+
+def small_graph(i: int, seed: int, n_lo: int = 50, n_hi: int = 5000):
+    """Graph i of a batch: n log-uniform in [n_lo, n_hi], mean out-degree
+    uniform in [4, 12], even i: directed ER, odd i: R-MAT on 2^ceil(log2 n)
+    nodes trimmed to n (about n * degree arcs kept)."""
+    u = uniforms(seed, 10_000_000 + i, 2)
+    n = int(round(np.exp(np.log(n_lo) + u[0] * (np.log(n_hi) - np.log(n_lo)))))
+    deg = 4.0 + 8.0 * u[1]
+    m = min(int(round(n * deg)), n * (n - 1))
+    if i % 2 == 0:
+        return er_graph(n, m, seed=seed * 1_000_003 + i)
+    scale = max(1, int(np.ceil(np.log2(n))))
+    # arcs landing inside [0, n)^2 are about a fraction (n / 2^scale)^2 of all (lower for skewed R-MAT);
+    # draw enough that about m survive the trim
+    frac = (n / float(1 << scale)) ** 2
+    return rmat_graph_arcs(scale, int(m / max(frac, 0.05)), seed * 1_000_003 + i, n_keep=n)
+
+
+def batch_pattern(i: int, seed: int, k_lo: int = 3, k_hi: int = 6):
+    """Pattern i of a batch: k uniform in [k_lo, k_hi], arc density rho
+    uniform in [0.3, 0.7], redrawn until weakly connected."""
+    u = uniforms(seed, 20_000_000 + i, 2)
+    k = k_lo + int(u[0] * (k_hi - k_lo + 1))
+    return random_pattern(min(k, k_hi), 0.3 + 0.4 * u[1], seed, 30_000_000 + i)

@@ -1,0 +1,67 @@
+"""Batched matching: every (pattern, graph) pair's count from one launch
+equals xm_count on that pair and the oracle; tunings, CUDA-graph replay and
+the autotuner do not change results."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xm():
+    import paper_2404_11105_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def setup(xm):
+    graphs = [synth.small_graph(i, seed=41, n_lo=20, n_hi=300) for i in range(10)]
+    pats = [synth.CYCLE3, synth.FFL, synth.BIFAN, synth.CYCLE4, synth.FFCHAIN5, (2, [(0, 1)])] + \
+           [synth.batch_pattern(i, seed=43, k_hi=5) for i in range(6)]
+    xg = [xm.Graph(*g) for g in graphs]
+    og = [oracle.OracleGraph(*g) for g in graphs]
+    xp = [xm.Plan(p) for p in pats]
+    pairs = [(pi, gi) for pi in range(len(pats)) for gi in range(len(graphs))]
+    return pats, xg, og, xp, pairs
+
+
+def test_batch_equals_single_and_oracle(xm, setup):
+    pats, xg, og, xp, pairs = setup
+    counts = xm.xm_count_batch(xp, xg, pairs)
+    for (pi, gi), c in zip(pairs, counts):
+        assert c == xm.xm_count(xg[gi], xp[pi]), (pi, gi)
+    # oracle on a subset of pairs (all patterns, first three graphs)
+    for (pi, gi), c in zip(pairs, counts):
+        if gi < 3:
+            assert c == og[gi].count_matches(pats[pi]), (pi, gi)
+
+
+def test_batch_tunings_graph_replay_and_autotuner(xm, setup):
+    pats, xg, og, xp, pairs = setup
+    ref = xm.xm_count_batch(xp, xg, pairs)
+    b = xm.Batch(xp, xg, pairs)
+    for t in (dict(window=64, unit=1, warps_per_block=2), dict(window=96, unit=7), dict(window=512, unit=128)):
+        b.set_tuning(**t)
+        b.run()
+        assert b.counts() == ref, t
+    # captured CUDA graph, replayed twice
+    b.run(graph=True)
+    assert b.counts() == ref
+    b.run(graph=True)
+    assert b.counts() == ref
+    best, ms = b.tune([(128, 16, 4, 0, 0), (256, 64, 8, 0, 0), (64, 4, 8, 2, 0)], reps=2)
+    assert ms > 0 and best in ({"window": 128, "unit": 16, "warps_per_block": 4, "blocks_per_sm": 0, "budget_ms": 0},
+                               {"window": 256, "unit": 64, "warps_per_block": 8, "blocks_per_sm": 0, "budget_ms": 0},
+                               {"window": 64, "unit": 4, "warps_per_block": 8, "blocks_per_sm": 2, "budget_ms": 0})
+    b.run()
+    assert b.counts() == ref
+    b.free()
+
+
+def test_batch_rejects_bad_pairs(xm, setup):
+    pats, xg, og, xp, pairs = setup
+    with pytest.raises(xm.XmError):
+        xm.Batch(xp, xg, [(0, len(xg))])

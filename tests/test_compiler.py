@@ -111,9 +111,26 @@ def test_shared_endpoints_are_reduced():
 def test_tuning_roundtrip_and_validation():
     p = xm.Plan(synth.BIFAN)
     p.set_tuning(window=256, unit=16, warps_per_block=4, blocks_per_sm=2)
-    assert p.tuning() == {"window": 256, "unit": 16, "warps_per_block": 4, "blocks_per_sm": 2}
+    assert p.tuning() == {"window": 256, "unit": 16, "warps_per_block": 4, "blocks_per_sm": 2, "budget_ms": 0}
     with pytest.raises(xm.XmError):
         p.set_tuning(window=100)
+
+
+DENSE = [synth.random_pattern(k, 0.9, 123, k) for k in (6, 7, 8)] + \
+        [(8, [(u, v) for u in range(8) for v in range(8) if u != v])]
+
+
+@pytest.mark.parametrize("pattern", DENSE)
+def test_dense_patterns_use_many_operands(pattern):
+    # a vertex with arcs both ways to every earlier vertex has 2(k-1) operands
+    k = pattern[0]
+    p = xm.Plan(pattern)
+    assert max(len(p.level(l)["ops"]) for l in range(k)) > 7
+    n, src, dst = synth.er_graph(12, 100, seed=2)
+    out, inn = adjacency_lists(n, src, dst)
+    g = oracle.OracleGraph(n, src, dst)
+    assert run_plan(n, out, inn, p) == g.count_matches(pattern)
+    assert run_plan(n, out, inn, xm.Plan(pattern, xm.XM_NO_REDUCE)) == g.count_matches(pattern)
 
 
 @pytest.mark.parametrize("seed", [3, 4])

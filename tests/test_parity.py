@@ -260,3 +260,17 @@ def test_s20_motifs_sampled_and_closed_forms(xm, s20):
         for v in roots:
             v = int(v)
             assert xm.xm_count_range(g, pe, v, v + 1) == og.count_embeddings(pat, pe.start, v, v + 1), (name, v)
+
+
+DENSE = [synth.random_pattern(k, 0.9, 123, k) for k in (6, 7, 8)] + \
+        [synth.random_pattern(6, 0.6, 7, s) for s in range(3)]
+
+
+@pytest.mark.parametrize("pattern", DENSE)
+def test_dense_patterns_many_operands(xm, rmat_tiny, pattern):
+    # levels with more than 7 operand lists (reciprocal arcs to many earlier levels)
+    g, og = rmat_tiny
+    want = og.count_matches(pattern)
+    for flags in (xm.XM_REDUCE, xm.XM_NO_REDUCE):
+        assert xm.xm_count(g, xm.Plan(pattern, flags)) == want
+    assert xm.xm_count_batch([xm.Plan(pattern)], [g], [(0, 0)]) == [want]
