@@ -216,6 +216,102 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------- serve arm ----
+
+def run_serve(args):
+    """Resident graphs, Poisson query arrivals, continuous batching into
+    slots (one stream each) vs the same queries one xm_count at a time."""
+    import torch
+    import paper_2404_11105_b300 as xm
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    graphs = [xm.Graph(*synth.rmat_graph(22, 16, seed=6))]
+    graphs += [xm.Graph(*synth.small_graph(i, seed=6, n_lo=100, n_hi=10000)) for i in range(args.serve_graphs)]
+    load_s = time.perf_counter() - t0
+    pool = [synth.batch_pattern(i, seed=66, k_hi=args.serve_kmax) for i in range(64)]
+    plans = []
+    for p in pool:
+        pl = xm.Plan(p)
+        pl.set_tuning(budget_ms=args.serve_budget_ms, blocks_per_sm=2)
+        plans.append(pl)
+
+    def requests(rate, seed):
+        n = int(min(4000, max(200, rate * args.serve_seconds)))
+        u = synth.uniforms(seed, 77, 3 * n).reshape(n, 3)
+        arrivals = np.cumsum(-np.log1p(-u[:, 0]) / rate)
+        pats = (u[:, 1] * len(plans)).astype(int)
+        tgt = np.where(u[:, 2] < 0.1, 0, 1 + (u[:, 2] * 1e6).astype(int) % args.serve_graphs)
+        return arrivals, pats, tgt
+
+    def serve(rate, seed):
+        arrivals, pats, tgt = requests(rate, seed)
+        srv = xm.Server(graphs, slots=args.serve_slots, mem_budget_bytes=120 << 30)
+        n = len(arrivals)
+        done_t = np.zeros(n)
+        status = np.zeros(n, int)
+        counts = [None] * n
+        nxt = 0
+        start = time.perf_counter()
+        finished = 0
+        while finished < n:
+            now = time.perf_counter() - start
+            while nxt < n and arrivals[nxt] <= now:
+                if not srv.submit(plans[pats[nxt]], int(tgt[nxt]), nxt):
+                    break
+                nxt += 1
+            for tag, c, st in srv.poll(wait=False):
+                done_t[tag] = time.perf_counter() - start
+                status[tag] = st
+                counts[tag] = c
+                finished += 1
+        srv.free()
+        lat = (done_t - arrivals) * 1000.0
+        ok = status == xm.XM_OK
+        return {"rate_req_s": rate, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "completed_per_s": n / done_t.max(),
+                "timeouts": int((status == xm.XM_ETIMEOUT).sum())}, counts, (arrivals, pats, tgt), ok
+
+    results = []
+    mixes = []
+    for i, rate in enumerate(int(r) for r in args.serve_rates.split(",")):
+        r, counts, req, ok = serve(rate, 100 + i)
+        results.append(r)
+        mixes.append((counts, req, ok))
+    # the highest rate's requests one xm_count at a time (same budgets)
+    counts, (arrivals, pats, tgt), ok = mixes[-1]
+    t1 = time.perf_counter()
+    same = 0
+    n_seq = min(len(pats), 300)
+    for q in range(n_seq):
+        try:
+            c = xm.xm_count(graphs[int(tgt[q])], plans[pats[q]])
+        except xm.XmError as e:
+            c = None
+            assert e.status == xm.XM_ETIMEOUT
+        if ok[q] and c is not None:
+            assert c == counts[q], "a query's count differs alone and in the mix"
+            same += 1
+    seq_s = time.perf_counter() - t1
+    seq_qps = n_seq / seq_s
+    best = max(r["completed_per_s"] for r in results)
+    line = {"metric": "queries/s", "value": best, "unit": "queries/s", "n_gpus": 1, "steps": len(results),
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "resident R-MAT scale 22 EF16 (seed 6) + %d small graphs (n log-uniform "
+                                   "100-10000, mean out-degree 4-12, seed 6); Poisson arrivals; random connected "
+                                   "patterns k 3-%d, density 0.3-0.7; target scale-22 graph w.p. 0.1"
+                                   % (args.serve_graphs, args.serve_kmax),
+                       "slots": args.serve_slots, "budget_ms_per_query": args.serve_budget_ms,
+                       "memory_budget_gb": 120, "graph_load_s": round(load_s, 1)},
+            "per_rate": results,
+            "sequential": {"queries_per_s": seq_qps, "queries": n_seq, "same_result_checked": same,
+                           "sample": "first %d requests of the highest-rate stream, one xm_count each" % n_seq},
+            "speedup_vs_sequential": best / seq_qps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------- batch arm ----
 
 def run_batch(args):
@@ -322,7 +418,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="xm", choices=["xm", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rmat24", "batch"])
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rmat24", "batch", "serve"])
+    ap.add_argument("--serve-graphs", type=int, default=1000)
+    ap.add_argument("--serve-rates", default="100,300,1000,3000,10000")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate")
+    ap.add_argument("--serve-budget-ms", type=int, default=200, help="device-time budget per query")
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-kmax", type=int, default=6)
     ap.add_argument("--batch-graphs", type=int, default=10000)
     ap.add_argument("--batch-patterns", type=int, default=256)
     ap.add_argument("--batch-single-sample", type=int, default=400,
@@ -338,6 +440,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
     import torch.distributed as dist

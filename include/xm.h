@@ -365,6 +365,49 @@ void xm_batch_free(xm_batch b);
 int xm_count_batch(int32_t np, const xm_plan *plans, int32_t ng, const xm_graph *graphs, int64_t npairs,
                    const int32_t *pair_pg, uint64_t *out_counts, void *stream);
 
+/* ------------------------------------------------------------- serving */
+
+/*
+ * Serving: graphs stay resident; count queries are admitted into one of a
+ * fixed number of slots when a slot is free and the query's scratch fits
+ * the memory budget; each slot runs its query's kernels on its own stream,
+ * so a query admitted while others are on the GPU overlaps with them
+ * (continuous batching driven by the caller's loop). Not in the paper.
+ *
+ * xm_query_bytes -- the admission estimate of a count query of plan p on
+ * graph g: the device scratch of the pipeline (about 4 bytes x (3n +
+ * 1.001m) plus control data). Intermediate partial matches are never
+ * materialised (bounded per-warp windows), so this is the whole
+ * per-query device footprint.
+ *
+ * xm_server_create -- ng graph handles (borrowed; they must outlive the
+ * server), nslots (1..256) concurrent queries, mem_budget_bytes the
+ * admission budget over the queries in flight.
+ *
+ * xm_server_submit -- try to admit a count query of plan p on graph
+ * `graph_index`, labelled `tag`. Never blocks: *admitted = 1 when it was
+ * enqueued, 0 when no slot or not enough budget is free now (retry after a
+ * poll). The plan is copied; its tuning applies (budget_ms bounds the
+ * query's device time: such a query completes with XM_ETIMEOUT).
+ * Errors: XM_EINVAL (bad index, or a query larger than the whole budget).
+ *
+ * xm_server_poll -- collect finished queries: up to max_results entries of
+ * tags[i], counts[2i..2i+1] (128-bit lo, hi) and status[i] (XM_OK or
+ * XM_ETIMEOUT); *n_done receives how many. wait != 0 first blocks until the
+ * oldest query in flight has finished.
+ *
+ * xm_server_info -- busy slots and scratch bytes in flight.
+ * xm_server_free -- waits for the queries in flight, then frees the server.
+ */
+typedef struct xm_server_s *xm_server;
+uint64_t xm_query_bytes(xm_graph g, xm_plan p);
+int xm_server_create(int32_t ng, const xm_graph *graphs, int32_t nslots, uint64_t mem_budget_bytes, xm_server *out);
+int xm_server_submit(xm_server s, xm_plan p, int32_t graph_index, int64_t tag, int32_t *admitted);
+int xm_server_poll(xm_server s, int32_t wait, int32_t max_results, int64_t *tags, uint64_t *counts, int32_t *status,
+                   int32_t *n_done);
+int xm_server_info(xm_server s, int32_t *busy_slots, uint64_t *bytes_in_flight);
+void xm_server_free(xm_server s);
+
 /*
  * xm_count_noalloc -- xm_count for callers that cannot allocate device
  * memory. The paper has no counterpart: this is a deployment variant of

@@ -27,7 +27,9 @@ EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_gr
            "xm_plan_describe", "xm_plan_free", "xm_plan_set_tuning", "xm_plan_get_tuning", "xm_count",
            "xm_count_range", "xm_count_stats", "xm_enumerate", "xm_enumerate_range", "xm_graph_last_timing",
            "xm_count_noalloc", "xm_batch_create", "xm_batch_set_tuning", "xm_batch_get_tuning", "xm_batch_run",
-           "xm_batch_run_graph", "xm_batch_counts", "xm_batch_tune", "xm_batch_free", "xm_count_batch"]
+           "xm_batch_run_graph", "xm_batch_counts", "xm_batch_tune", "xm_batch_free", "xm_count_batch",
+           "xm_query_bytes", "xm_server_create", "xm_server_submit", "xm_server_poll", "xm_server_info",
+           "xm_server_free"]
 
 
 class XmError(RuntimeError):
@@ -93,6 +95,12 @@ def _load():
                                          ctypes.POINTER(ctypes.c_float), vp]),
         "xm_batch_free": (None, [vp]),
         "xm_count_batch": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64, i32p, u64p, vp]),
+        "xm_query_bytes": (ctypes.c_uint64, [vp, vp]),
+        "xm_server_create": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.c_uint64, ctypes.POINTER(vp)]),
+        "xm_server_submit": (ctypes.c_int, [vp, vp, i32, i64, i32p]),
+        "xm_server_poll": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(ctypes.c_int64), u64p, i32p, i32p]),
+        "xm_server_info": (ctypes.c_int, [vp, i32p, u64p]),
+        "xm_server_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -339,3 +347,55 @@ def xm_count_batch(plans, graphs, pairs, stream=None):
         return b.counts(stream)
     finally:
         b.free()
+
+
+def xm_query_bytes(g: Graph, p: Plan) -> int:
+    """Admission estimate (device scratch bytes) of a count query."""
+    return int(lib().xm_query_bytes(g._h, p._h))
+
+
+class Server:
+    """Resident graphs + slots; queries are admitted by scratch memory and
+    overlap on the GPU (one stream per slot)."""
+
+    def __init__(self, graphs, slots: int = 8, mem_budget_bytes: int = 120 << 30):
+        self._graphs = list(graphs)
+        ga = (ctypes.c_void_p * len(self._graphs))(*[g._h.value for g in self._graphs])
+        h = ctypes.c_void_p()
+        _check(lib().xm_server_create(len(self._graphs), ga, slots, mem_budget_bytes, ctypes.byref(h)))
+        self._h = h
+        self.slots = slots
+
+    def submit(self, plan: Plan, graph_index: int, tag: int) -> bool:
+        adm = ctypes.c_int32()
+        _check(lib().xm_server_submit(self._h, plan._h, graph_index, tag, ctypes.byref(adm)))
+        return bool(adm.value)
+
+    def poll(self, wait: bool = False, max_results: int = 256):
+        """[(tag, count or None, status)] of finished queries."""
+        tags = (ctypes.c_int64 * max_results)()
+        counts = (ctypes.c_uint64 * (2 * max_results))()
+        st = (ctypes.c_int32 * max_results)()
+        n = ctypes.c_int32()
+        _check(lib().xm_server_poll(self._h, 1 if wait else 0, max_results, tags, counts, st, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            c = (counts[2 * i + 1] << 64) | counts[2 * i] if st[i] == XM_OK else None
+            out.append((tags[i], c, st[i]))
+        return out
+
+    def info(self):
+        b, by = ctypes.c_int32(), ctypes.c_uint64()
+        _check(lib().xm_server_info(self._h, ctypes.byref(b), ctypes.byref(by)))
+        return b.value, by.value
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().xm_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -326,21 +326,29 @@ __device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g,
     level_bounds(L, ws.m, lo, hi);
     ListRef lists[XM_MAXOPS + 1];
     int cnt = 0;
+    // lane i fetches operand i's list bounds and hash table, all in parallel
+    ListRef mine{nullptr, 0, 0, nullptr, 0};
+    if (lane < L.nops) mine = op_list(g, L.op_dir[lane], ws.m[L.op_level[lane]]);
     bool use_reuse = (L.reuse >= 1) && ws.st[L.reuse].complete;
     if (use_reuse && __popc(L.reuse_ops) == 1) {
         // a reused set that equals its single operand list adds nothing but
         // loses the list's hash index: take the list instead
-        const int i = __ffs(L.reuse_ops) - 1;
-        const ListRef r = op_list(g, L.op_dir[i], ws.m[L.op_level[i]]);
-        if (r.len == ws.st[L.reuse].set_len) use_reuse = false;
+        const int len_i = __shfl_sync(FULL, mine.len, __ffs(L.reuse_ops) - 1);
+        if (len_i == ws.st[L.reuse].set_len) use_reuse = false;
     }
     if (use_reuse) {
         const LvState& R = ws.st[L.reuse];
         lists[cnt++] = {R.set_ptr, R.set_len, R.set_shared, nullptr, 0};
     }
     for (int i = 0; i < L.nops; i++) {
+        ListRef r;
+        r.p = reinterpret_cast<const int32_t*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.p), i));
+        r.len = __shfl_sync(FULL, mine.len, i);
+        r.shared = 0;
+        r.tab = reinterpret_cast<const int32_t*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.tab), i));
+        r.T = __shfl_sync(FULL, mine.T, i);
         if (use_reuse && ((L.reuse_ops >> i) & 1u)) continue;
-        lists[cnt++] = op_list(g, L.op_dir[i], ws.m[L.op_level[i]]);
+        lists[cnt++] = r;
     }
     int d = 0;
     bool empty = false;
