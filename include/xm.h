@@ -92,7 +92,8 @@ int xm_version(void);
  *
  * Builds a dual sorted CSR (out-lists and in-lists, each ascending, int32
  * offsets) on the host and copies it to device memory owned by the handle,
- * together with the handle's scratch buffers (about 4 bytes per node).
+ * together with the handle's scratch buffers (about 12 bytes per node and
+ * 12 bytes per arc) and a hash index of the lists (up to 16 bytes per arc).
  * Errors: XM_EINVAL for n/m out of range or an id outside [0, n), or more
  * than 2^31-1 arcs after deduplication; XM_ENOMEM; XM_ECUDA.
  */
@@ -288,6 +289,22 @@ int xm_count_stats(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint
 int xm_enumerate(xm_graph g, xm_plan p, int32_t *dev_out, uint64_t capacity, uint64_t *total,
                  uint64_t *written, void *stream);
 
+/*
+ * xm_count_roots / xm_enumerate_roots -- as xm_count / xm_enumerate,
+ * restricted to the matches whose start vertex is mapped to one of the
+ * given nodes (the paper's runs from a given percentage of start nodes,
+ * Sec. 6.4). roots: host array of nroots node ids in [0, n) (copied; sorted
+ * and deduplicated by the call). Counts over a partition of the nodes add
+ * up to xm_count. Errors: XM_EINVAL for an id outside [0, n) or nroots > n.
+ */
+int xm_count_roots(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroots, uint64_t *lo, uint64_t *hi,
+                   void *stream);
+int xm_enumerate_roots(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroots, int32_t *dev_out,
+                       uint64_t capacity, uint64_t *total, uint64_t *written, void *stream);
+/* xm_count_roots with the xm_count_stats counters. */
+int xm_count_roots_stats(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroots, uint64_t *lo, uint64_t *hi,
+                         xm_stats *stats, void *stream);
+
 /* xm_enumerate restricted to start nodes in [root_lo, root_hi). */
 int xm_enumerate_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, int32_t *dev_out,
                        uint64_t capacity, uint64_t *total, uint64_t *written, void *stream);
@@ -376,7 +393,7 @@ int xm_count_batch(int32_t np, const xm_plan *plans, int32_t ng, const xm_graph 
  *
  * xm_query_bytes -- the admission estimate of a count query of plan p on
  * graph g: the device scratch of the pipeline (about 4 bytes x (3n +
- * 1.001m) plus control data). Intermediate partial matches are never
+ * 3.001m) plus control data). Intermediate partial matches are never
  * materialised (bounded per-warp windows), so this is the whole
  * per-query device footprint.
  *
@@ -433,7 +450,7 @@ void xm_server_free(xm_server s);
  *   stream    stream for the kernels; the call synchronises it.
  *
  * Limits and errors: XM_EINVAL when the scratch the graph needs (about
- * 4 bytes x (3n + 1.001m) plus small control data) exceeds
+ * 4 bytes x (3n + 3.001m) plus small control data) exceeds
  * XM_NOALLOC_SCRATCH_BYTES -- use xm_count then --, or for NULL/invalid
  * sizes; XM_ECUDA when a CUDA call fails.
  * Set-up: the first call on each device looks up the scratch array's device

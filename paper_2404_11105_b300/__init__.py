@@ -29,7 +29,7 @@ EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_gr
            "xm_count_noalloc", "xm_batch_create", "xm_batch_set_tuning", "xm_batch_get_tuning", "xm_batch_run",
            "xm_batch_run_graph", "xm_batch_counts", "xm_batch_tune", "xm_batch_free", "xm_count_batch",
            "xm_query_bytes", "xm_server_create", "xm_server_submit", "xm_server_poll", "xm_server_info",
-           "xm_server_free"]
+           "xm_server_free", "xm_count_roots", "xm_enumerate_roots", "xm_count_roots_stats"]
 
 
 class XmError(RuntimeError):
@@ -96,6 +96,9 @@ def _load():
         "xm_batch_free": (None, [vp]),
         "xm_count_batch": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64, i32p, u64p, vp]),
         "xm_query_bytes": (ctypes.c_uint64, [vp, vp]),
+        "xm_count_roots": (ctypes.c_int, [vp, vp, i32p, i64, u64p, u64p, vp]),
+        "xm_count_roots_stats": (ctypes.c_int, [vp, vp, i32p, i64, u64p, u64p, ctypes.POINTER(xm_stats), vp]),
+        "xm_enumerate_roots": (ctypes.c_int, [vp, vp, i32p, i64, vp, ctypes.c_uint64, u64p, u64p, vp]),
         "xm_server_create": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.c_uint64, ctypes.POINTER(vp)]),
         "xm_server_submit": (ctypes.c_int, [vp, vp, i32, i64, i32p]),
         "xm_server_poll": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(ctypes.c_int64), u64p, i32p, i32p]),
@@ -399,3 +402,32 @@ class Server:
             self.free()
         except Exception:
             pass
+
+
+def xm_count_roots(g: Graph, p: Plan, roots, stream=None) -> int:
+    """Matches whose start vertex maps to one of `roots` (host int array)."""
+    r = np.ascontiguousarray(roots, np.int32)
+    lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().xm_count_roots(g._h, p._h, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(r),
+                                ctypes.byref(lo), ctypes.byref(hi), _stream(stream)))
+    return (hi.value << 64) | lo.value
+
+
+def xm_enumerate_roots(g: Graph, p: Plan, roots, out, capacity: int | None = None, stream=None):
+    r = np.ascontiguousarray(roots, np.int32)
+    cap = out.numel() // p.k if capacity is None else capacity
+    total, written = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib().xm_enumerate_roots(g._h, p._h, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(r), _ptr(out),
+                                  cap, ctypes.byref(total), ctypes.byref(written), _stream(stream))
+    if rc not in (XM_OK, XM_EOVERFLOW):
+        _check(rc)
+    return total.value, written.value, rc == XM_EOVERFLOW
+
+
+def xm_count_roots_stats(g: Graph, p: Plan, roots, stream=None):
+    r = np.ascontiguousarray(roots, np.int32)
+    lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
+    st = xm_stats()
+    _check(lib().xm_count_roots_stats(g._h, p._h, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(r),
+                                      ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(st), _stream(stream)))
+    return (hi.value << 64) | lo.value, {f: getattr(st, f) for f, _ in xm_stats._fields_ if f != "reserved"}

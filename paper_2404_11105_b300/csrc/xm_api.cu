@@ -51,10 +51,13 @@ static void free_graph(xm_graph_s* g) {
     cudaFree(g->d_out_htab);
     cudaFree(g->d_in_hoff);
     cudaFree(g->d_in_htab);
+    cudaFree(g->d_roots);
     cudaFree(g->d_root_chunks);
     cudaFree(g->d_chunk_cnt);
     cudaFree(g->d_l1set);
     cudaFree(g->d_units);
+    cudaFree(g->d_l1root);
+    cudaFree(g->d_e_units);
     cudaFree(g->d_block_sums);
     cudaFree(g->d_ctl);
     for (auto& e : g->ev)
@@ -70,7 +73,8 @@ static XmPlanDev* ctl_plan(xm_graph_s* g) {
 }
 
 static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int32_t* out, uint64_t capacity,
-               uint64_t* lo, uint64_t* hi, xm_stats* stats, uint64_t* written, cudaStream_t stream) {
+               uint64_t* lo, uint64_t* hi, xm_stats* stats, uint64_t* written, cudaStream_t stream,
+               const int32_t* roots = nullptr, int64_t nroots = 0) {
     if (!g || !p || !lo || !hi) { set_error("NULL argument"); return XM_EINVAL; }
     if (mode == MODE_EMIT && capacity > 0 && !out) { set_error("NULL output buffer"); return XM_EINVAL; }
     int cur = -1;
@@ -87,12 +91,18 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
     a.chunk_cnt = g->d_chunk_cnt;
     a.l1set = g->d_l1set;
     a.units = g->d_units;
+    a.l1root = g->d_l1root;
+    a.e_units = g->d_e_units;
+    a.emax = (int32_t)std::max<int64_t>(g->m, 1);
+    a.l2_units = use_l2_units(P.dev) ? 1 : 0;
     a.block_sums = g->d_block_sums;
     a.n_block_sums = g->n_block_sums;
     a.ctl = g->d_ctl;
     a.cmax = (int32_t)g->cmax;
     a.r_lo = (int32_t)std::min<int64_t>(r_lo, g->n);
     a.r_hi = (int32_t)std::max<int64_t>(r_hi, a.r_lo);
+    a.root_list = roots;
+    a.n_idx = roots ? (int32_t)nroots : g->n;
     a.unit = t.unit;
     a.window = t.window;
     a.out = out;
@@ -125,7 +135,7 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
         stats->units = ctl[CTL_STATS + 3];
         stats->leaf_elems = ctl[CTL_STATS + 4];
         // start-node degree checks: 16 B per node in range
-        stats->alg_bytes += 16ull * (uint64_t)(a.r_hi - a.r_lo);
+        stats->alg_bytes += 16ull * (uint64_t)(roots ? nroots : (int64_t)(a.r_hi - a.r_lo));
     }
     if (mode == MODE_EMIT && ctl[CTL_EMIT] > capacity) {
         set_error("enumeration buffer too small");
@@ -189,7 +199,8 @@ int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, 
         const size_t adj_b = (size_t)std::max<int64_t>(H.m, 1) * sizeof(int32_t);
         g->cmax = chunk_capacity(n, H.m);
         if (g->cmax >= INT32_MAX) { delete g; set_error("graph too large for the chunk index"); return XM_EINVAL; }
-        g->n_block_sums = (std::max<int64_t>((int64_t)n + 1, g->cmax + 1) + SCAN_TILE - 1) / SCAN_TILE;
+        g->n_block_sums = (std::max<int64_t>(std::max<int64_t>((int64_t)n + 1, g->cmax + 1), H.m + 2) + SCAN_TILE - 1) /
+                          SCAN_TILE;
         cudaError_t e = cudaSuccess;
         if (e == cudaSuccess) e = cudaMalloc(&g->d_out_off, off_b);
         if (e == cudaSuccess) e = cudaMalloc(&g->d_in_off, off_b);
@@ -199,6 +210,8 @@ int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, 
         if (e == cudaSuccess) e = cudaMalloc(&g->d_chunk_cnt, (size_t)(g->cmax + 1) * sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMalloc(&g->d_l1set, adj_b);
         if (e == cudaSuccess) e = cudaMalloc(&g->d_units, off_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_l1root, adj_b);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_e_units, adj_b + sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMalloc(&g->d_block_sums, g->n_block_sums * sizeof(int64_t));
         if (e == cudaSuccess) e = cudaMalloc(&g->d_ctl, ctl_bytes());
         for (auto& ev : g->ev)
@@ -383,6 +396,67 @@ int xm_count_stats(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint
                    xm_stats* stats, void* stream) {
     if (!stats) { set_error("NULL stats"); return XM_EINVAL; }
     return run(g, p, MODE_STATS, root_lo, root_hi, nullptr, 0, lo, hi, stats, nullptr, (cudaStream_t)stream);
+}
+
+// Uploads a validated, sorted, repeat-free copy of a host root list into the
+// graph's root buffer (allocated on first use).
+static int stage_roots(xm_graph g, const int32_t* roots, int64_t nroots, int64_t* kept, cudaStream_t stream) {
+    if (!roots || nroots < 0 || nroots > g->n) { set_error("bad root list"); return XM_EINVAL; }
+    std::vector<int32_t> r(roots, roots + nroots);
+    for (int32_t v : r)
+        if (v < 0 || v >= g->n) { set_error("root id outside [0, n)"); return XM_EINVAL; }
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    if (!g->d_roots) XM_CUDA(cudaMalloc(&g->d_roots, (size_t)g->n * sizeof(int32_t)), "root buffer");
+    if (!r.empty())
+        XM_CUDA(cudaMemcpyAsync(g->d_roots, r.data(), r.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream),
+                "root upload");
+    XM_CUDA(cudaStreamSynchronize(stream), "root upload");
+    *kept = (int64_t)r.size();
+    return XM_OK;
+}
+
+int xm_count_roots(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, uint64_t* lo, uint64_t* hi,
+                   void* stream) {
+    if (!g || !p || !lo || !hi) { set_error("NULL argument"); return XM_EINVAL; }
+    int64_t kept = 0;
+    int rc = stage_roots(g, roots, nroots, &kept, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (kept == 0) { *lo = *hi = 0; return XM_OK; }
+    return run(g, p, MODE_COUNT, 0, INT32_MAX, nullptr, 0, lo, hi, nullptr, nullptr, (cudaStream_t)stream, g->d_roots,
+               kept);
+}
+
+int xm_count_roots_stats(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, uint64_t* lo, uint64_t* hi,
+                         xm_stats* stats, void* stream) {
+    if (!g || !p || !lo || !hi || !stats) { set_error("NULL argument"); return XM_EINVAL; }
+    int64_t kept = 0;
+    int rc = stage_roots(g, roots, nroots, &kept, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (kept == 0) {
+        *lo = *hi = 0;
+        memset(stats, 0, sizeof *stats);
+        return XM_OK;
+    }
+    return run(g, p, MODE_STATS, 0, INT32_MAX, nullptr, 0, lo, hi, stats, nullptr, (cudaStream_t)stream, g->d_roots,
+               kept);
+}
+
+int xm_enumerate_roots(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, int32_t* dev_out,
+                       uint64_t capacity, uint64_t* total, uint64_t* written, void* stream) {
+    if (!g || !p || !total || !written) { set_error("NULL argument"); return XM_EINVAL; }
+    int64_t kept = 0;
+    int rc = stage_roots(g, roots, nroots, &kept, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (kept == 0) { *total = *written = 0; return XM_OK; }
+    uint64_t lo = 0, hi = 0, w = 0;
+    rc = run(g, p, MODE_EMIT, 0, INT32_MAX, dev_out, capacity, &lo, &hi, nullptr, &w, (cudaStream_t)stream,
+             g->d_roots, kept);
+    if (rc == XM_OK || rc == XM_EOVERFLOW) {
+        *total = lo;
+        *written = w;
+    }
+    return rc;
 }
 
 int xm_enumerate_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, int32_t* dev_out,

@@ -63,10 +63,13 @@ struct xm_graph_s {
     // scratch of the matching pipeline (see xm_kernels.cu): first-level
     // chunk counts and offsets, first-level candidate sets, work units, scan
     // partials, and a small control block (counters, accumulators, plan)
+    int32_t* d_roots = nullptr;        // n: explicit start nodes (allocated on first use)
     int32_t* d_root_chunks = nullptr;  // n + 1
     int32_t* d_chunk_cnt = nullptr;    // cmax + 1
     int32_t* d_l1set = nullptr;        // max(m, 1)
     int32_t* d_units = nullptr;        // n + 1
+    int32_t* d_l1root = nullptr;       // max(m, 1): start-node index of each first-level candidate
+    int32_t* d_e_units = nullptr;      // max(m, 1) + 1: work units per first-level candidate
     int64_t* d_block_sums = nullptr;
     unsigned long long* d_ctl = nullptr;
     int64_t n_block_sums = 0;

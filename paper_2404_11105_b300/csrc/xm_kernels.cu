@@ -223,22 +223,28 @@ __device__ __forceinline__ void plan_to_smem(XmPlanDev& P, const XmPlanDev* __re
     __syncthreads();
 }
 
+// Start node of index i (the root list, or the node itself).
+__device__ __forceinline__ int32_t root_node(const RunArgs& ra, int i) {
+    return ra.root_list ? __ldg(ra.root_list + i) : i;
+}
+
 // Chunks of the first-level driver list per start node (0 when the node
 // fails the start vertex's degree filter or lies outside [r_lo, r_hi)).
 __global__ void k_l1_chunks(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     __shared__ XmPlanDev P;
     plan_to_smem(P, plan_g);
     const GraphDev& g = ra.g;
-    const int n = g.n;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
+    const int ni = ra.n_idx;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= ni; i += gridDim.x * blockDim.x) {
         int c = 0;
-        if (v < n && v >= ra.r_lo && v < ra.r_hi && passes_degree(g, v, P.lv[0].dout_min, P.lv[0].din_min)) {
+        const int v = i < ni ? root_node(ra, i) : -1;
+        if (i < ni && v >= ra.r_lo && v < ra.r_hi && passes_degree(g, v, P.lv[0].dout_min, P.lv[0].din_min)) {
             ListRef d, o;
             int no, c0, c1;
             first_level_lists(P, g, v, d, o, no, c0, c1);
             c = (c1 - c0 + L1_CHUNK - 1) / L1_CHUNK;
         }
-        ra.root_chunks[v] = c;
+        ra.root_chunks[i] = c;
     }
 }
 
@@ -249,9 +255,9 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
     __shared__ XmPlanDev P;
     plan_to_smem(P, plan_g);
     const GraphDev& g = ra.g;
-    const int n = g.n;
+    const int ni = ra.n_idx;
     const int lane = threadIdx.x & 31;
-    const int total = __ldg(ra.root_chunks + n);
+    const int total = __ldg(ra.root_chunks + ni);
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const bool filter_deg = P.k > 2;
     const XmLevel& L1 = P.lv[1];
@@ -261,8 +267,9 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
             if (!WRITE && lane == 0) ra.chunk_cnt[c] = 0;
             continue;
         }
-        const int v = owner_of(ra.root_chunks, n, c);
-        const int j = c - __ldg(ra.root_chunks + v);
+        const int vi = owner_of(ra.root_chunks, ni, c);
+        const int v = root_node(ra, vi);
+        const int j = c - __ldg(ra.root_chunks + vi);
         ListRef d, o;
         int no, c0, c1;
         first_level_lists(P, g, v, d, o, no, c0, c1);
@@ -293,7 +300,11 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
             }
             if (ok && filter_deg) ok = passes_degree(g, x, L1.dout_min, L1.din_min);
             const unsigned mask = __ballot_sync(FULL, ok);
-            if (WRITE && ok) out[cnt + __popc(mask & ((1u << lane) - 1))] = x;
+            if (WRITE && ok) {
+                const int at = cnt + __popc(mask & ((1u << lane) - 1));
+                out[at] = x;
+                ra.l1root[ra.chunk_cnt[c] + at] = vi;
+            }
             cnt += __popc(mask);
         }
         if (!WRITE && lane == 0) ra.chunk_cnt[c] = cnt;
@@ -303,7 +314,7 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
 
 // Work units per start node: its first-level set cut into `unit` pieces.
 __global__ void k_units(RunArgs ra) {
-    const int n = ra.g.n;
+    const int n = ra.n_idx;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
         int u = 0;
         if (v < n) {
@@ -482,11 +493,19 @@ __device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, 
 template <int MODE>
 __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane,
                                          const RunArgs& ra, unsigned long long& stat_bytes,
-                                         unsigned long long& leaf_elems) {
+                                         unsigned long long& leaf_elems, int ra_pos = 0, int ra_len = -1) {
     stat_bytes += setup_level<MODE>(P, g, ws, l, lane);
     LvState& S = ws.st[l];
     if (S.empty) return 0;
-    const int pos = S.c0, end = S.c1;
+    // optional sub-range [c0 + ra_pos, c0 + ra_pos + ra_len) of the cut driver range
+    const int pos = ra_len < 0 ? S.c0 : min(S.c1, S.c0 + ra_pos);
+    const int end = ra_len < 0 ? S.c1 : min(S.c1, pos + ra_len);
+    if (pos >= end) return 0;
+    if (ra_len >= 0 && lane == 0) {
+        S.drv_pos = pos;
+        S.drv_end = end;
+    }
+    __syncwarp();
     if (MODE == MODE_STATS && lane == 0) leaf_elems += end - pos;
     const XmLevel& L = P.lv[l];
     if (MODE != MODE_EMIT && S.nprobe == 0) {
@@ -535,11 +554,11 @@ __device__ bool descend(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
 // the last level is counted (or emitted) into acc.
 template <int MODE>
 __device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* wins, int W, int wl0, int lane,
-                        const RunArgs& ra, unsigned long long& acc, Stats& st, const Budget& budget) {
+                        const RunArgs& ra, unsigned long long& acc, Stats& st, const Budget& budget, int l0 = 1) {
     const int k = P.k;
-    int l = 1;
+    int l = l0;
     unsigned steps = 0;
-    while (l >= 1) {
+    while (l >= l0) {
         if ((++steps & 255u) == 0 && budget.expired(lane)) return false;
         LvState& S = ws.st[l];
         if (S.wpos >= S.it_hi) {
@@ -607,6 +626,72 @@ __device__ __forceinline__ void grab_units(unsigned long long* head, long long t
     cnt = __shfl_sync(FULL, c, 0);
 }
 
+// Start of start node i's first-level set in l1set.
+__device__ __forceinline__ int set_start(const RunArgs& ra, int i) {
+    return __ldg(ra.chunk_cnt + __ldg(ra.root_chunks + i));
+}
+
+// Second-level driver and its cut range for the partial match (m0, m1),
+// computed by one thread exactly as setup_level does it for a warp: the
+// same lists in the same order (the first level's complete set in place of
+// the operands it covers, unless it equals its single operand list), the
+// first shortest list as driver, the cut by the order bounds.
+__device__ void level2_cut(const XmPlanDev& P, const GraphDev& g, int32_t m0, int32_t m1, const int32_t* set_ptr,
+                           int set_len, int& c0, int& c1) {
+    const XmLevel& L = P.lv[2];
+    const int32_t m[2] = {m0, m1};
+    int32_t lo = -1, hi = INT_MAX;
+    for (uint32_t a = L.lo_mask; a; a &= a - 1) lo = max(lo, m[__ffs(a) - 1]);
+    for (uint32_t b = L.hi_mask; b; b &= b - 1) hi = min(hi, m[__ffs(b) - 1]);
+    bool use_reuse = L.reuse == 1;
+    if (use_reuse && __popc(L.reuse_ops) == 1) {
+        const int i = __ffs(L.reuse_ops) - 1;
+        if (op_list(g, L.op_dir[i], m[L.op_level[i]]).len == set_len) use_reuse = false;
+    }
+    const int32_t* dp = nullptr;
+    int dlen = INT_MAX;
+    bool empty = false;
+    if (use_reuse) {
+        dp = set_ptr;
+        dlen = set_len;
+        if (set_len == 0) empty = true;
+    }
+    for (int i = 0; i < L.nops; i++) {
+        if (use_reuse && ((L.reuse_ops >> i) & 1u)) continue;
+        const ListRef r = op_list(g, L.op_dir[i], m[L.op_level[i]]);
+        if (r.len == 0) empty = true;
+        if (r.len < dlen) { dp = r.p; dlen = r.len; }
+    }
+    c0 = 0;
+    c1 = dlen;
+    if (!empty) {
+        if (lo >= 0) c0 = lbound(dp, 0, c1, lo + 1, false);
+        if (hi != INT_MAX) c1 = lbound(dp, c0, c1, hi, false);
+    }
+    if (empty || c1 < c0) c1 = c0;
+}
+
+// Work units per first-level candidate (patterns of three or more
+// vertices): its second-level driver range cut into pieces, so the work
+// below one hub is spread over many warps. One thread per candidate.
+__global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+    __shared__ XmPlanDev P;
+    plan_to_smem(P, plan_g);
+    const int E = set_start(ra, ra.n_idx);
+    const int per = P.k == 3 ? LEAF_UNIT : ra.unit;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= ra.emax; e += gridDim.x * blockDim.x) {
+        int u = 0;
+        if (e < E) {
+            const int i = __ldg(ra.l1root + e);
+            const int s0 = set_start(ra, i), s1 = set_start(ra, i + 1);
+            int c0, c1;
+            level2_cut(P, ra.g, root_node(ra, i), __ldg(ra.l1set + e), ra.l1set + s0, s1 - s0, c0, c1);
+            u = (c1 - c0 + per - 1) / per;
+        }
+        ra.e_units[e] = u;
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -622,34 +707,75 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
     WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase);
     int32_t* wins = reinterpret_cast<int32_t*>(wbase + align16(sizeof(WarpSmem)));  // level l >= 2 at (l-2)*W
     const GraphDev& g = ra.g;
-    const int n = g.n;
-    const int total = ra.units[n];
+    const bool two_level = !ra.l2_units;
+    // unit index space: pieces of a start node's first-level set, or pieces
+    // of a first-level candidate's second-level driver range
+    const int32_t* uprefix = two_level ? ra.units : ra.e_units;
+    const int nidx = two_level ? ra.n_idx : ra.emax;
+    const int total = uprefix[nidx];
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int per2 = k == 3 ? LEAF_UNIT : ra.unit;
 
     unsigned long long acc = 0;
     Stats st;
     Budget budget;
     budget.start(ra.ctl, ra.budget_ns, lane);
-    int root = -1;
+    int owner = -1;
     for (;;) {
         long long start;
         int cnt;
         grab_units(ra.ctl + CTL_HEAD, total, nwarps, lane, start, cnt, budget);
         if (cnt <= 0) break;
-        for (int u = (int)start; u < (int)start + cnt; u++) {
-            if (root < 0 || u < __ldg(ra.units + root) || u >= __ldg(ra.units + root + 1)) root = owner_of(ra.units, n, u);
-            const int chunk = u - __ldg(ra.units + root);
-            const int s0 = __ldg(ra.chunk_cnt + __ldg(ra.root_chunks + root));
-            const int s1 = __ldg(ra.chunk_cnt + __ldg(ra.root_chunks + root + 1));
-            const int32_t* base = ra.l1set + s0;
-            const int a = chunk * ra.unit;
-            const int b = min(s1 - s0, a + ra.unit);
-            if (MODE == MODE_STATS && lane == 0) {
-                st.units++;
-                st.bytes += 4ull * (b - a);
+        bool stop = false;
+        for (int u = (int)start; u < (int)start + cnt && !stop; u++) {
+            if (owner < 0 || u < __ldg(uprefix + owner) || u >= __ldg(uprefix + owner + 1)) {
+                // consecutive units usually belong to the next owners: step a
+                // few ahead before searching
+                int o = owner;
+                bool found = false;
+                if (o >= 0 && u >= __ldg(uprefix + o))
+                    for (int t = 0; t < 4 && o + 1 < nidx; t++) {
+                        o++;
+                        if (u < __ldg(uprefix + o + 1)) { found = u >= __ldg(uprefix + o); break; }
+                    }
+                owner = found ? o : owner_of(uprefix, nidx, u);
             }
-            if (k == 2) {
+            const int chunk = u - __ldg(uprefix + owner);
+            if (MODE == MODE_STATS && lane == 0) st.units++;
+            if (two_level && k > 2) {
+                // unit = (start node, a piece of its first-level set)
+                const int root = owner;
+                const int s0 = set_start(ra, root), s1 = set_start(ra, root + 1);
+                const int32_t* base = ra.l1set + s0;
+                const int a = chunk * ra.unit;
+                const int b = min(s1 - s0, a + ra.unit);
+                if (MODE == MODE_STATS && lane == 0) st.bytes += 4ull * (b - a);
+                if (lane == 0) {
+                    ws.m[0] = root_node(ra, root);
+                    LvState& S1 = ws.st[1];
+                    S1.it_ptr = base;
+                    S1.it_shared = 0;
+                    S1.wpos = a;
+                    S1.it_hi = b;
+                    S1.set_ptr = base;
+                    S1.set_len = s1 - s0;
+                    S1.set_shared = 0;
+                    S1.complete = 1;
+                    S1.drv_pos = S1.drv_end = 0;
+                }
+                __syncwarp();
+                if (!explore<MODE>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget, 1)) stop = true;
+                continue;
+            }
+            if (two_level) {
                 // the first level is the last: every candidate is a match
+                const int root = owner;
+                const int s0 = set_start(ra, root), s1 = set_start(ra, root + 1);
+                const int32_t* base = ra.l1set + s0;
+                const int a = chunk * ra.unit;
+                const int b = min(s1 - s0, a + ra.unit);
+                const int32_t rnode = root_node(ra, root);
+                if (MODE == MODE_STATS && lane == 0) st.bytes += 4ull * (b - a);
                 if (MODE == MODE_EMIT) {
                     for (int p = a; p < b; p += 32) {
                         const bool ok = p + lane < b;
@@ -658,7 +784,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                         if (lane == 0) o = atomicAdd(ra.ctl + CTL_EMIT, (unsigned long long)__popc(mask));
                         o = __shfl_sync(FULL, o, 0) + lane;
                         if (ok && o < ra.capacity) {
-                            ra.out[o * 2 + P.order[0]] = root;
+                            ra.out[o * 2 + P.order[0]] = rnode;
                             ra.out[o * 2 + P.order[1]] = __ldg(base + p + lane);
                         }
                     }
@@ -666,22 +792,58 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                 if (lane == 0) acc += b - a;
                 continue;
             }
+            // unit = (start node, one first-level candidate, a piece of the
+            // second level's driver range)
+            const int e = owner;
+            const int root = __ldg(ra.l1root + e);
+            const int s0 = set_start(ra, root), s1 = set_start(ra, root + 1);
             if (lane == 0) {
-                ws.m[0] = root;
+                ws.m[0] = root_node(ra, root);
+                ws.m[1] = __ldg(ra.l1set + e);
                 LvState& S1 = ws.st[1];
-                S1.it_ptr = base;
-                S1.it_shared = 0;
-                S1.wpos = a;
-                S1.it_hi = b;
-                S1.set_ptr = base;
+                S1.set_ptr = ra.l1set + s0;
                 S1.set_len = s1 - s0;
                 S1.set_shared = 0;
                 S1.complete = 1;
+                S1.wpos = S1.it_hi = 0;
                 S1.drv_pos = S1.drv_end = 0;
             }
             __syncwarp();
-            if (!explore<MODE>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget)) break;
+            if (MODE == MODE_STATS && lane == 0) st.ext++;
+            if (k == 3) {
+                acc += leaf_level<MODE>(P, g, ws, 2, lane, ra, st.bytes, st.leaf, chunk * per2, per2);
+                if (MODE == MODE_STATS && lane == 0) st.sets++;
+                continue;
+            }
+            st.bytes += setup_level<MODE>(P, g, ws, 2, lane);
+            if (MODE == MODE_STATS && lane == 0) st.sets++;
+            LvState& S2 = ws.st[2];
+            if (S2.empty) continue;
+            const int pos = min(S2.c1, S2.c0 + chunk * per2);
+            const int end = min(S2.c1, pos + per2);
+            if (pos >= end) continue;
+            const bool whole = pos == S2.c0 && end == S2.c1;
+            if (lane == 0) {
+                S2.drv_pos = pos;
+                S2.drv_end = end;
+            }
+            __syncwarp();
+            int32_t* win = wins;  // level 2's window
+            scan_level<MODE, true>(P, g, ws, S2, 2, win, W, lane, ra, st.bytes);
+            if (lane == 0) {
+                S2.complete = whole && S2.drv_pos >= S2.drv_end;
+                S2.it_ptr = win;
+                S2.it_shared = 1;
+                S2.wpos = 0;
+                S2.it_hi = S2.wcnt;
+                S2.set_ptr = win;
+                S2.set_len = S2.wcnt;
+                S2.set_shared = 1;
+            }
+            __syncwarp();
+            if (!explore<MODE>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget, 2)) stop = true;
         }
+        if (stop) break;
     }
     flush_count(acc, ra.ctl + CTL_COUNT_LO, lane);
     if (MODE == MODE_STATS && lane == 0) {
@@ -900,10 +1062,20 @@ cudaError_t launch_batch(const BatchDev& b, int warps_per_block, int blocks_per_
     return cudaGetLastError();
 }
 
+bool use_l2_units(const XmPlanDev& P) {
+    if (P.k < 3) return false;
+    if (P.k > 3) return true;
+    // three vertices: split below the first level only when the last level
+    // intersects lists (a single list is counted in O(log) per candidate)
+    const XmLevel& L = P.lv[2];
+    const int lists = (L.reuse >= 1 ? 1 : 0) + L.nops - (L.reuse >= 1 ? __builtin_popcount(L.reuse_ops) : 0);
+    return lists > 1;
+}
+
 cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev, const RunArgs& a,
                          int warps_per_block, int blocks_per_sm, cudaStream_t stream, cudaEvent_t* ev) {
     cudaError_t err;
-    const int64_t len = (int64_t)a.g.n + 1;
+    const int64_t len = (int64_t)a.n_idx + 1;
     int dev = 0, nsm = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
@@ -919,9 +1091,16 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
         k_l1<false, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, a);
     if ((err = scan_in_place(a.chunk_cnt, (int64_t)a.cmax + 1, a, stream)) != cudaSuccess) return err;
     k_l1<true, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, a);
-    // 2. work units
-    k_units<<<grid_nodes, 256, 0, stream>>>(a);
-    if ((err = scan_in_place(a.units, len, a, stream)) != cudaSuccess) return err;
+    // 2. work units: per start node for two-vertex patterns, else per
+    // first-level candidate (pieces of the second level's driver range)
+    if (!a.l2_units) {
+        k_units<<<grid_nodes, 256, 0, stream>>>(a);
+        if ((err = scan_in_place(a.units, len, a, stream)) != cudaSuccess) return err;
+    } else {
+        const int grid_e = (int)std::min<int64_t>(((int64_t)a.emax + 256) / 256, (int64_t)nsm * 16);
+        k_l2_units<<<grid_e, 256, 0, stream>>>(plan_dev, a);
+        if ((err = scan_in_place(a.e_units, (int64_t)a.emax + 1, a, stream)) != cudaSuccess) return err;
+    }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // 3. persistent matcher
     const size_t smem = match_smem_bytes(P.k, a.window, warps_per_block);

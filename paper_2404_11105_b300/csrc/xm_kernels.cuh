@@ -66,12 +66,18 @@ struct RunArgs {
     int32_t* root_chunks;       // n + 1: first-level driver chunks per start node, scanned
     int32_t* chunk_cnt;         // cmax + 1: survivors per chunk, scanned into set offsets
     int32_t* l1set;             // first-level candidate sets of all start nodes
-    int32_t* units;             // n + 1: work units per start node, scanned
+    int32_t* units;             // n + 1: work units per start node, scanned (two-level patterns)
+    int32_t* l1root;            // per first-level candidate: index of its start node
+    int32_t* e_units;           // emax + 1: work units per first-level candidate, scanned
+    int32_t emax;               // capacity of l1set / l1root (>= any number of first-level candidates)
+    int32_t l2_units;           // 1: work units per first-level candidate; 0: per start node
     int64_t* block_sums;        // scan partials
     int64_t n_block_sums;
     unsigned long long* ctl;    // control block
     int32_t cmax;               // chunk_cnt has cmax + 1 entries
     int32_t r_lo, r_hi;         // start-node range
+    const int32_t* root_list;   // optional explicit start nodes (null: all nodes 0..n-1)
+    int32_t n_idx;              // start-node index space: n, or the root-list length
     int32_t unit;               // first-level candidates per work unit
     int32_t window;             // candidate window per deeper level (ids)
     unsigned long long budget_ns;  // matcher time budget (0: none)
@@ -107,12 +113,18 @@ cudaError_t launch_batch(const BatchDev& b, int warps_per_block, int blocks_per_
 constexpr int SCAN_TILE = 4096;
 // First-level driver positions per chunk of the first-level set build.
 constexpr int L1_CHUNK = 1024;
+// Second-level driver positions per work unit when the second level is the
+// last one (three-vertex patterns): leaf intersections are cheap per id.
+constexpr int LEAF_UNIT = 1024;
 
 // Upper bound on the number of first-level chunks of a graph.
 int64_t chunk_capacity(int32_t n, int64_t m);
 
 // Bytes of shared memory a block of `warps` warps needs.
 size_t match_smem_bytes(int k, int window, int warps);
+
+// Whether a plan's work units split below the first level (RunArgs::l2_units).
+bool use_l2_units(const XmPlanDev& P);
 
 // Enqueues the whole matching pass on `stream`: first-level sets, work
 // units, persistent matcher. `plan_dev` is a device copy of the plan.

@@ -66,16 +66,19 @@ extern "C" int xm_count_noalloc(const int32_t* out_off, const int32_t* out_adj, 
         return XM_EINVAL;
     }
     // scratch layout, each piece 256-byte aligned: root_chunks[n+1],
-    // chunk_cnt[cmax+1], l1set[max(m,1)], units[n+1], block sums, control
-    // block (counters + plan copy)
+    // chunk_cnt[cmax+1], l1set[max(m,1)], l1root[max(m,1)], units[n+1],
+    // e_units[max(m,1)+1], block sums, control block (counters + plan copy)
     const int64_t cmax = chunk_capacity(n, m);
-    const int64_t n_block_sums = (std::max<int64_t>((int64_t)n + 1, cmax + 1) + SCAN_TILE - 1) / SCAN_TILE;
+    const int64_t emax = std::max<int64_t>(m, 1);
+    const int64_t n_block_sums =
+        (std::max<int64_t>(std::max<int64_t>((int64_t)n + 1, cmax + 1), emax + 1) + SCAN_TILE - 1) / SCAN_TILE;
     const size_t b_nodes = align256(((size_t)n + 1) * sizeof(int32_t));
     const size_t b_chunks = align256((size_t)(cmax + 1) * sizeof(int32_t));
-    const size_t b_l1 = align256((size_t)std::max<int64_t>(m, 1) * sizeof(int32_t));
+    const size_t b_l1 = align256((size_t)emax * sizeof(int32_t));
+    const size_t b_e = align256((size_t)(emax + 1) * sizeof(int32_t));
     const size_t b_sums = align256((size_t)n_block_sums * sizeof(int64_t));
     const size_t b_ctl = align256(CTL_WORDS * sizeof(unsigned long long)) + align256(sizeof(XmPlanDev));
-    const size_t need = 2 * b_nodes + b_chunks + b_l1 + b_sums + b_ctl;
+    const size_t need = 2 * b_nodes + b_chunks + 2 * b_l1 + b_e + b_sums + b_ctl;
     if (need > (size_t)XM_NOALLOC_SCRATCH_BYTES) {
         set_error("graph too large for the fixed scratch area of xm_count_noalloc (needs " + std::to_string(need) +
                   " bytes, has " + std::to_string((size_t)XM_NOALLOC_SCRATCH_BYTES) + "); use xm_count");
@@ -91,7 +94,11 @@ extern "C" int xm_count_noalloc(const int32_t* out_off, const int32_t* out_adj, 
     a.root_chunks = reinterpret_cast<int32_t*>(q); q += b_nodes;
     a.chunk_cnt = reinterpret_cast<int32_t*>(q); q += b_chunks;
     a.l1set = reinterpret_cast<int32_t*>(q); q += b_l1;
+    a.l1root = reinterpret_cast<int32_t*>(q); q += b_l1;
     a.units = reinterpret_cast<int32_t*>(q); q += b_nodes;
+    a.e_units = reinterpret_cast<int32_t*>(q); q += b_e;
+    a.emax = (int32_t)emax;
+    a.l2_units = use_l2_units(p->plan.dev) ? 1 : 0;
     a.block_sums = reinterpret_cast<int64_t*>(q); q += b_sums;
     a.ctl = reinterpret_cast<unsigned long long*>(q);
     XmPlanDev* plan_dev = reinterpret_cast<XmPlanDev*>(q + align256(CTL_WORDS * sizeof(unsigned long long)));
@@ -99,6 +106,8 @@ extern "C" int xm_count_noalloc(const int32_t* out_off, const int32_t* out_adj, 
     a.cmax = (int32_t)cmax;
     a.r_lo = 0;
     a.r_hi = n;
+    a.root_list = nullptr;
+    a.n_idx = n;
     a.unit = p->tuning.unit;
     a.window = p->tuning.window;
     a.out = nullptr;

@@ -35,21 +35,24 @@ constexpr size_t kHostBytes = kHostCtl + xm::CTL_WORDS * sizeof(unsigned long lo
 
 // scratch layout of one query (same pieces as a graph handle's scratch)
 struct Layout {
-    size_t nodes, chunks, l1, sums, ctl, plan, total;
-    int64_t cmax, n_block_sums;
+    size_t nodes, chunks, l1, e, sums, ctl, plan, total;
+    int64_t cmax, emax, n_block_sums;
 };
 
 Layout layout_for(int32_t n, int64_t m) {
     Layout L;
     L.cmax = xm::chunk_capacity(n, m);
-    L.n_block_sums = (std::max<int64_t>((int64_t)n + 1, L.cmax + 1) + xm::SCAN_TILE - 1) / xm::SCAN_TILE;
+    L.emax = std::max<int64_t>(m, 1);
+    L.n_block_sums = (std::max<int64_t>(std::max<int64_t>((int64_t)n + 1, L.cmax + 1), L.emax + 1) +
+                      xm::SCAN_TILE - 1) / xm::SCAN_TILE;
     L.nodes = align256(((size_t)n + 1) * sizeof(int32_t));
     L.chunks = align256((size_t)(L.cmax + 1) * sizeof(int32_t));
-    L.l1 = align256((size_t)std::max<int64_t>(m, 1) * sizeof(int32_t));
+    L.l1 = align256((size_t)L.emax * sizeof(int32_t));
+    L.e = align256((size_t)(L.emax + 1) * sizeof(int32_t));
     L.sums = align256((size_t)L.n_block_sums * sizeof(int64_t));
     L.ctl = align256(xm::CTL_WORDS * sizeof(unsigned long long));
     L.plan = align256(sizeof(XmPlanDev));
-    L.total = 2 * L.nodes + L.chunks + L.l1 + L.sums + L.ctl + L.plan;
+    L.total = 2 * L.nodes + L.chunks + 2 * L.l1 + L.e + L.sums + L.ctl + L.plan;
     return L;
 }
 
@@ -156,7 +159,11 @@ int xm_server_submit(xm_server s, xm_plan p, int32_t graph_index, int64_t tag, i
     a.root_chunks = reinterpret_cast<int32_t*>(q); q += L.nodes;
     a.chunk_cnt = reinterpret_cast<int32_t*>(q); q += L.chunks;
     a.l1set = reinterpret_cast<int32_t*>(q); q += L.l1;
+    a.l1root = reinterpret_cast<int32_t*>(q); q += L.l1;
     a.units = reinterpret_cast<int32_t*>(q); q += L.nodes;
+    a.e_units = reinterpret_cast<int32_t*>(q); q += L.e;
+    a.emax = (int32_t)L.emax;
+    a.l2_units = use_l2_units(p->plan.dev) ? 1 : 0;
     a.block_sums = reinterpret_cast<int64_t*>(q); q += L.sums;
     a.ctl = reinterpret_cast<unsigned long long*>(q); q += L.ctl;
     XmPlanDev* plan_dev = reinterpret_cast<XmPlanDev*>(q);
@@ -164,6 +171,8 @@ int xm_server_submit(xm_server s, xm_plan p, int32_t graph_index, int64_t tag, i
     a.cmax = (int32_t)L.cmax;
     a.r_lo = 0;
     a.r_hi = g->n;
+    a.root_list = nullptr;
+    a.n_idx = g->n;
     a.unit = p->tuning.unit;
     a.window = p->tuning.window;
     a.budget_ns = (unsigned long long)p->tuning.budget_ms * 1000000ull;
