@@ -438,6 +438,8 @@ def main():
     ap.add_argument("--root-sample", type=int, default=1024,
                     help="rmat24: count over a seeded uniform sample of 1/N of the start nodes")
     ap.add_argument("--budget-ms", type=int, default=0, help="device-time budget per count call (0: none)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time every pattern with its unreduced plan (no candidate-set reuse)")
     ap.add_argument("--enum-capacity", type=int, default=1 << 24,
                     help="rmat24: matches written by the untimed enumeration check")
     args = ap.parse_args()
@@ -557,6 +559,28 @@ def main():
                 "kernel": "k_match (persistent matcher)", "kernel_share_of_step":
                     sum(kernel_ms) / sum(step_ms)}
 
+    ablation = None
+    if args.ablation:
+        # reduced plan vs the plan over the original pattern (no reduction,
+        # no reuse): device time, algorithmic bytes, equal counts
+        ablation = {}
+        for name, pat in pats.items():
+            row = {}
+            for label, flags in (("reduced", xm.XM_REDUCE), ("unreduced", xm.XM_NO_REDUCE)):
+                p = xm.Plan(pat, flags)
+                ms_ = []
+                for _ in range(3):
+                    c = count_one(p)
+                    ms_.append(sum(g.last_timing()))
+                assert c == counts[name]
+                if roots is not None:
+                    _, st = xm.xm_count_roots_stats(g, p, roots)
+                else:
+                    _, st = xm.xm_count_stats(g, p, r_lo, r_hi)
+                row[label] = {"ms": round(min(ms_), 3), "alg_bytes": st["alg_bytes"], "reuse_levels": p.n_reuse}
+            row["speedup"] = round(row["unreduced"]["ms"] / row["reduced"]["ms"], 3)
+            ablation[name] = row
+
     enum = None
     if roots is not None and args.enum_capacity > 0:
         # enumeration into a device buffer (untimed): the first pattern
@@ -612,7 +636,7 @@ def main():
                        "parallelism": f"start-node shards x{world}" if world > 1 else "1 GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": LAUNCHES_PER_CALL * launches, "clocks": clocks,
-            "counts": {k: int(v) for k, v in counts.items()}, "enumeration": enum,
+            "counts": {k: int(v) for k, v in counts.items()}, "enumeration": enum, "ablation": ablation,
             "device_ms_per_pattern": {k: round(statistics.median(v), 3) for k, v in per_pattern_ms.items()}}
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -11,7 +11,9 @@ What it computes (see the C file header for the full statement):
   * embeddings: injective maps m with (m(u), m(v)) an arc for every pattern
     arc (u, v) -- non-induced matching;
   * matches: embeddings modulo Aut(P), represented by the orbit-smallest
-    tuple; #matches = #embeddings / |Aut(P)|.
+    tuple; #matches = #embeddings / |Aut(P)|;
+  * with induced=True, non-arcs of the pattern must be non-arcs among the
+    matched nodes (induced subgraph isomorphism).
 
 Parity pins for every function here live in ``tests/test_oracle.py``
 (brute force over all node tuples, closed forms, invariants).
@@ -60,12 +62,12 @@ def _L():
         lib.og_aut.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_void_p]
         lib.og_aut.restype = ctypes.c_int
         lib.og_count_embeddings.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i32p, i32p,
-                                            ctypes.c_int, ctypes.c_int32, ctypes.c_int32, u64ref, u64ref]
+                                            ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, u64ref, u64ref]
         lib.og_count_embeddings.restype = ctypes.c_int
-        lib.og_count_matches.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i32p, i32p,
+        lib.og_count_matches.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int,
                                          u64ref, u64ref]
         lib.og_count_matches.restype = ctypes.c_int
-        lib.og_enumerate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i32p, i32p,
+        lib.og_enumerate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_int64]
         lib.og_enumerate.restype = ctypes.c_int64
         lib.og_canonicalize.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int64, i32p, i32p]
@@ -118,31 +120,33 @@ class OracleGraph:
     def has_arc(self, u: int, v: int) -> bool:
         return bool(_L().og_has_arc(self._h, u, v))
 
-    def count_embeddings(self, pattern, root: int = 0, r_lo: int = 0, r_hi: int | None = None) -> int:
-        """Embeddings m with m(root) in [r_lo, r_hi)."""
+    def count_embeddings(self, pattern, root: int = 0, r_lo: int = 0, r_hi: int | None = None,
+                         induced: bool = False) -> int:
+        """Embeddings m with m(root) in [r_lo, r_hi) (induced: non-arcs too)."""
         k, e, ps, pd = _pattern_arrays(pattern)
         lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
         r_hi = self.n if r_hi is None else r_hi
-        if _L().og_count_embeddings(self._h, k, e, ps, pd, root, r_lo, r_hi, ctypes.byref(lo), ctypes.byref(hi)):
+        if _L().og_count_embeddings(self._h, k, e, ps, pd, root, r_lo, r_hi, int(induced), ctypes.byref(lo),
+                                    ctypes.byref(hi)):
             raise ValueError("bad pattern")
         return (hi.value << 64) | lo.value
 
-    def count_matches(self, pattern) -> int:
+    def count_matches(self, pattern, induced: bool = False) -> int:
         """Distinct matched subgraphs (orbit-smallest embeddings)."""
         k, e, ps, pd = _pattern_arrays(pattern)
         lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
-        if _L().og_count_matches(self._h, k, e, ps, pd, ctypes.byref(lo), ctypes.byref(hi)):
+        if _L().og_count_matches(self._h, k, e, ps, pd, int(induced), ctypes.byref(lo), ctypes.byref(hi)):
             raise ValueError("bad pattern")
         return (hi.value << 64) | lo.value
 
-    def enumerate(self, pattern, capacity: int | None = None) -> np.ndarray:
+    def enumerate(self, pattern, capacity: int | None = None, induced: bool = False) -> np.ndarray:
         """All matches as an (N, k) int32 array, each row the orbit-smallest
         embedding in pattern-vertex order, rows sorted lexicographically."""
         k, e, ps, pd = _pattern_arrays(pattern)
         if capacity is None:
-            capacity = int(_L().og_enumerate(self._h, k, e, ps, pd, None, 0))
+            capacity = int(_L().og_enumerate(self._h, k, e, ps, pd, int(induced), None, 0))
         buf = np.empty(max(capacity, 1) * k, np.int32)
-        total = int(_L().og_enumerate(self._h, k, e, ps, pd, buf.ctypes.data, capacity))
+        total = int(_L().og_enumerate(self._h, k, e, ps, pd, int(induced), buf.ctypes.data, capacity))
         rows = buf[: min(total, capacity) * k].reshape(-1, k)
         return sort_rows(rows)
 

@@ -17,6 +17,10 @@
  *     the automorphism group Aut(P); the matches are the embeddings that are
  *     lexicographically smallest within their orbit, and
  *     #matches = #embeddings / |Aut(P)|.
+ * Induced variant (the induced-subgraph reading of "isomorphic and oriented
+ * the same", Sec. 2): additionally, for every ordered pair of pattern
+ * vertices (u, v) WITHOUT a pattern arc, (m(u), m(v)) must NOT be an arc;
+ * a match is then a node set whose induced subgraph is isomorphic to P.
  * The matcher is single-threaded backtracking over the original (unreduced)
  * pattern, visiting pattern vertices in breadth-first order from a chosen
  * root vertex, checking every pattern arc to an already matched vertex by
@@ -171,6 +175,7 @@ typedef struct {
     int parent_out[OG_MAXK];   /* 1: arc parent -> v (scan parent's out-list), 0: arc v -> parent */
     int32_t m[OG_MAXK];        /* m[v] = data node matched to pattern vertex v */
     int32_t r_lo, r_hi;        /* allowed data nodes for the root vertex */
+    int induced;               /* 1: non-arcs of the pattern must be non-arcs of G */
     /* match output */
     int unique_only;
     int naut;
@@ -221,6 +226,13 @@ static int consistent(const og_search *s, int d, int v, int32_t x) {
         int a = s->ps[i], b = s->pd[i];
         if (a == v && s->pos[b] < d && !has_arc(s->g, x, s->m[b])) return 0;
         if (b == v && s->pos[a] < d && !has_arc(s->g, s->m[a], x)) return 0;
+    }
+    if (s->induced) {
+        for (int j = 0; j < d; j++) {
+            int u = s->order[j];
+            if (!pattern_arc(s->k, s->e, s->ps, s->pd, u, v) && has_arc(s->g, s->m[u], x)) return 0;
+            if (!pattern_arc(s->k, s->e, s->ps, s->pd, v, u) && has_arc(s->g, x, s->m[u])) return 0;
+        }
     }
     return 1;
 }
@@ -273,9 +285,10 @@ static void extend(og_search *s, int d) {
 }
 
 static int setup(og_search *s, const og_graph *g, int k, int e, const int32_t *ps, const int32_t *pd,
-                 int root, int32_t r_lo, int32_t r_hi) {
+                 int root, int32_t r_lo, int32_t r_hi, int induced) {
     if (k < 1 || k > OG_MAXK || root < 0 || root >= k) return -1;
     memset(s, 0, sizeof *s);
+    s->induced = induced;
     s->g = g; s->k = k; s->e = e; s->ps = ps; s->pd = pd;
     s->r_lo = r_lo < 0 ? 0 : r_lo;
     s->r_hi = r_hi > g->n ? g->n : r_hi;
@@ -286,9 +299,9 @@ static int setup(og_search *s, const og_graph *g, int k, int e, const int32_t *p
 /* Number of embeddings whose root pattern vertex maps into [r_lo, r_hi), as
  * a 128-bit value (lo, hi). */
 int og_count_embeddings(const og_graph *g, int k, int e, const int32_t *ps, const int32_t *pd, int root,
-                        int32_t r_lo, int32_t r_hi, uint64_t *lo, uint64_t *hi) {
+                        int32_t r_lo, int32_t r_hi, int induced, uint64_t *lo, uint64_t *hi) {
     og_search s;
-    if (setup(&s, g, k, e, ps, pd, root, r_lo, r_hi)) return -1;
+    if (setup(&s, g, k, e, ps, pd, root, r_lo, r_hi, induced)) return -1;
     extend(&s, 0);
     *lo = (uint64_t)s.count;
     *hi = (uint64_t)(s.count >> 64);
@@ -296,10 +309,10 @@ int og_count_embeddings(const og_graph *g, int k, int e, const int32_t *ps, cons
 }
 
 /* Number of matches (embeddings that are the smallest of their Aut-orbit). */
-int og_count_matches(const og_graph *g, int k, int e, const int32_t *ps, const int32_t *pd,
+int og_count_matches(const og_graph *g, int k, int e, const int32_t *ps, const int32_t *pd, int induced,
                      uint64_t *lo, uint64_t *hi) {
     og_search s;
-    if (setup(&s, g, k, e, ps, pd, 0, 0, g->n)) return -1;
+    if (setup(&s, g, k, e, ps, pd, 0, 0, g->n, induced)) return -1;
     int32_t *aut = (int32_t *)malloc(40320 * OG_MAXK * sizeof(int32_t));
     if (!aut) return -1;
     s.naut = og_aut(k, e, ps, pd, aut);
@@ -315,10 +328,10 @@ int og_count_matches(const og_graph *g, int k, int e, const int32_t *ps, const i
 /* Writes up to `capacity` matches (k node ids each, in pattern-vertex order,
  * each the orbit-smallest embedding) in search order; returns the total
  * number of matches. */
-int64_t og_enumerate(const og_graph *g, int k, int e, const int32_t *ps, const int32_t *pd,
+int64_t og_enumerate(const og_graph *g, int k, int e, const int32_t *ps, const int32_t *pd, int induced,
                      int32_t *out, int64_t capacity) {
     og_search s;
-    if (setup(&s, g, k, e, ps, pd, 0, 0, g->n)) return -1;
+    if (setup(&s, g, k, e, ps, pd, 0, 0, g->n, induced)) return -1;
     int32_t *aut = (int32_t *)malloc(40320 * OG_MAXK * sizeof(int32_t));
     if (!aut) return -1;
     s.naut = og_aut(k, e, ps, pd, aut);

@@ -252,3 +252,71 @@ def test_synth_is_deterministic():
     assert n == 2000 and len(src) == 20000
     assert len({(int(u), int(v)) for u, v in zip(src, dst)}) == 20000
     assert not np.any(src == dst)
+
+
+# ------------------------------------------------------ induced variant --
+
+def brute_force_induced(n, arcs, pattern):
+    """(#embeddings, set of image node sets): every ordered pair of pattern
+    vertices is an arc of the pattern iff its image is an arc of G."""
+    k, parcs = pattern
+    pset = set(parcs)
+    emb = 0
+    images = set()
+    for t in itertools.product(range(n), repeat=k):
+        if len(set(t)) != k:
+            continue
+        if all(((t[u], t[v]) in arcs) == ((u, v) in pset) for u in range(k) for v in range(k) if u != v):
+            emb += 1
+            images.add(frozenset(t))
+    return emb, images
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("pattern", SMALL_PATTERNS + [synth.FFCHAIN5])
+def test_induced_oracle_vs_brute_force(seed, pattern):
+    n, src, dst = random_small_graph(7 if pattern[0] <= 4 else 6, 0.45, 50 + seed)
+    arcs = simple_arcs(n, src, dst)
+    emb, images = brute_force_induced(n, arcs, pattern)
+    g = oracle.OracleGraph(n, src, dst)
+    assert g.count_embeddings(pattern, induced=True) == emb
+    assert g.count_matches(pattern, induced=True) == len(images)
+    rows = g.enumerate(pattern, induced=True)
+    assert {frozenset(int(x) for x in r) for r in rows} == images
+
+
+def motif_containment():
+    """C[i][j] = non-induced matches of motif i inside motif j (as a graph)."""
+    names = list(synth.MOTIFS3)
+    C = np.zeros((13, 13), dtype=object)
+    for j, nj in enumerate(names):
+        k, arcs = synth.MOTIFS3[nj]
+        g = oracle.OracleGraph(3, np.array([a for a, _ in arcs], np.int32), np.array([b for _, b in arcs], np.int32))
+        for i, ni in enumerate(names):
+            C[i, j] = g.count_matches(synth.MOTIFS3[ni])
+    return names, C
+
+
+def test_motif_census_identities():
+    # induced counts of the 13 classes partition the weakly connected node
+    # triples; non-induced counts follow from them through the containment
+    # matrix (unitriangular once motifs are sorted by arc count)
+    names, C = motif_containment()
+    assert all(C[i, i] == 1 for i in range(13))
+    order = sorted(range(13), key=lambda i: len(synth.MOTIFS3[names[i]][1]))
+    for a in range(13):
+        for b in range(a):
+            assert C[order[a], order[b]] == 0  # a sparser motif never contains a denser one
+    n, src, dst = random_small_graph(11, 0.3, 9)
+    arcs = simple_arcs(n, src, dst)
+    und = {frozenset(a) for a in arcs}
+    connected_triples = 0
+    for t in itertools.combinations(range(n), 3):
+        pairs = [frozenset((t[i], t[j])) for i in range(3) for j in range(i + 1, 3)]
+        if sum(p in und for p in pairs) >= 2:
+            connected_triples += 1
+    g = oracle.OracleGraph(n, src, dst)
+    induced = np.array([g.count_matches(synth.MOTIFS3[nm], induced=True) for nm in names], dtype=object)
+    plain = np.array([g.count_matches(synth.MOTIFS3[nm]) for nm in names], dtype=object)
+    assert sum(induced) == connected_triples
+    assert list(C.dot(induced)) == list(plain)
