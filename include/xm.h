@@ -57,7 +57,10 @@ enum {
     XM_REDUCE = 0,     /* default: plan from the reduced pattern (Alg. 1, Sec. 5.1-5.2) */
     XM_NO_REDUCE = 1,  /* plan over the original pattern, no reuse of candidate sets
                           (the "XMiner without reduction" variant of Sec. 6.3) */
-    XM_EMBEDDINGS = 2  /* count every embedding; no symmetry-breaking conditions */
+    XM_EMBEDDINGS = 2, /* count every embedding; no symmetry-breaking conditions */
+    XM_INDUCED = 4     /* induced matching: a pair of pattern vertices without an arc must map to a
+                          pair of nodes without that arc (DIFF operands); the paper defines only
+                          edge and degree constraints, so this is an extension */
 };
 
 typedef struct xm_graph_s *xm_graph;
@@ -135,7 +138,7 @@ void xm_graph_free(xm_graph g);
  *   k          pattern vertices, 2 <= k <= 8 (vertices are 0..k-1).
  *   e          pattern arcs, 1 <= e <= k(k-1).
  *   psrc, pdst arc endpoints (host memory), e int32 each.
- *   flags      XM_REDUCE (0) | XM_NO_REDUCE | XM_EMBEDDINGS.
+ *   flags      XM_REDUCE (0) | XM_NO_REDUCE | XM_EMBEDDINGS | XM_INDUCED.
  *   out        receives the plan handle.
  * Errors: XM_EINVAL for a self-loop, a repeated arc, an id outside [0, k),
  * k or e out of range, or a pattern that is not weakly connected.
@@ -190,6 +193,9 @@ typedef struct {
     uint32_t lo_mask;
     uint32_t hi_mask;
     uint32_t neq_mask;
+    int32_t ndiff;          /* induced plans: lists the candidate must NOT be in */
+    int32_t diff_level[14];
+    int32_t diff_dir[14];
 } xm_level_info;
 
 int xm_plan_level(xm_plan p, int32_t level, xm_level_info *out);

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libxm.so")
 
 XM_OK, XM_EINVAL, XM_ENOMEM, XM_EOVERFLOW, XM_ECUDA, XM_ETIMEOUT, XM_EBUSY = range(7)
-XM_REDUCE, XM_NO_REDUCE, XM_EMBEDDINGS = 0, 1, 2
+XM_REDUCE, XM_NO_REDUCE, XM_EMBEDDINGS, XM_INDUCED = 0, 1, 2, 4
 
 # every symbol include/xm.h declares
 EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_graph_info", "xm_graph_csr",
@@ -52,7 +52,8 @@ class xm_level_info(ctypes.Structure):
     _fields_ = [("vertex", ctypes.c_int32), ("nops", ctypes.c_int32), ("op_level", ctypes.c_int32 * 14),
                 ("op_dir", ctypes.c_int32 * 14), ("reuse", ctypes.c_int32), ("reuse_ops", ctypes.c_uint32),
                 ("dout_min", ctypes.c_int32), ("din_min", ctypes.c_int32), ("lo_mask", ctypes.c_uint32),
-                ("hi_mask", ctypes.c_uint32), ("neq_mask", ctypes.c_uint32)]
+                ("hi_mask", ctypes.c_uint32), ("neq_mask", ctypes.c_uint32), ("ndiff", ctypes.c_int32),
+                ("diff_level", ctypes.c_int32 * 14), ("diff_dir", ctypes.c_int32 * 14)]
 
 
 def _load():
@@ -213,7 +214,8 @@ class Plan:
         return {"vertex": info.vertex, "ops": [(info.op_level[i], info.op_dir[i]) for i in range(info.nops)],
                 "reuse": info.reuse, "reuse_ops": info.reuse_ops, "dout_min": info.dout_min,
                 "din_min": info.din_min, "lo_mask": info.lo_mask, "hi_mask": info.hi_mask,
-                "neq_mask": info.neq_mask}
+                "neq_mask": info.neq_mask,
+                "diffs": [(info.diff_level[i], info.diff_dir[i]) for i in range(info.ndiff)]}
 
     def describe(self) -> str:
         need = lib().xm_plan_describe(self._h, None, 0)

@@ -346,6 +346,11 @@ int xm_plan_level(xm_plan p, int32_t level, xm_level_info* out) {
     out->lo_mask = L.lo_mask;
     out->hi_mask = L.hi_mask;
     out->neq_mask = L.neq_mask;
+    out->ndiff = L.ndiff;
+    for (int i = 0; i < L.ndiff; i++) {
+        out->diff_level[i] = L.diff_level[i];
+        out->diff_dir[i] = L.diff_dir[i];
+    }
     return XM_OK;
 }
 

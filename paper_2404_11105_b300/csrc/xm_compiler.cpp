@@ -270,7 +270,7 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
     if (k < 2 || k > XM_MAXK) { err = "k must be in [2, 8]"; return XM_EINVAL; }
     if (e < 1 || e > k * (k - 1)) { err = "arc count out of range"; return XM_EINVAL; }
     if (!psrc || !pdst) { err = "NULL arc array"; return XM_EINVAL; }
-    if (flags & ~(XM_NO_REDUCE | XM_EMBEDDINGS)) { err = "unknown flag"; return XM_EINVAL; }
+    if (flags & ~(XM_NO_REDUCE | XM_EMBEDDINGS | XM_INDUCED)) { err = "unknown flag"; return XM_EINVAL; }
     Pat P;
     P.k = k;
     P.e = e;
@@ -346,6 +346,15 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
             if (less[v] >> u & 1u) L.hi_mask |= 1u << j;  // m(v) < m(u)
         }
         if (l > 0 && L.nops == 0) { err = "internal: plan level without an operand list"; return XM_EINVAL; }
+        if (flags & XM_INDUCED) {
+            // induced matching: every missing pattern arc to an earlier level
+            // becomes a list the candidate must not be in
+            for (int j = 0; j < l; j++) {
+                int u = order[j];
+                if (!P.arc(u, v)) { L.diff_level[L.ndiff] = j; L.diff_dir[L.ndiff] = XM_DIR_OUT; L.ndiff++; }
+                if (!P.arc(v, u)) { L.diff_level[L.ndiff] = j; L.diff_dir[L.ndiff] = XM_DIR_IN; L.ndiff++; }
+            }
+        }
         L.neq_mask = ((1u << l) - 1) & ~adj_levels & ~L.lo_mask & ~L.hi_mask;
     }
     // Candidate-set reuse (Sec. 5.2): level l starts from the stored set of an
@@ -383,6 +392,16 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
                     if (el >= 0 && er >= 0 && (incl[er] & bit(el))) included = true;
                 }
                 if (!subset || !included || Rl.nops == 0) continue;
+                // a reused set was filtered by its own difference lists: they
+                // must all be differences of the reusing level too
+                bool diffs_ok = true;
+                for (int i = 0; i < Rl.ndiff && diffs_ok; i++) {
+                    bool found = false;
+                    for (int q = 0; q < L.ndiff; q++)
+                        if (L.diff_level[q] == Rl.diff_level[i] && L.diff_dir[q] == Rl.diff_dir[i]) found = true;
+                    diffs_ok = found;
+                }
+                if (!diffs_ok) continue;
                 bool bounds_ok = true;
                 for (int j = 0; j < r && bounds_ok; j++) {
                     int u = order[j];
@@ -458,9 +477,14 @@ std::string describe_plan(const Plan& p) {
             snprintf(buf, sizeof buf, " %s(L%d)", L.op_dir[i] == XM_DIR_OUT ? "out" : "in", L.op_level[i]);
             s += buf;
         }
-        snprintf(buf, sizeof buf, " reuse=%d/0x%x lo=0x%x hi=0x%x neq=0x%x\n", L.reuse, L.reuse_ops, L.lo_mask,
+        snprintf(buf, sizeof buf, " reuse=%d/0x%x lo=0x%x hi=0x%x neq=0x%x", L.reuse, L.reuse_ops, L.lo_mask,
                  L.hi_mask, L.neq_mask);
         s += buf;
+        for (int i = 0; i < L.ndiff; i++) {
+            snprintf(buf, sizeof buf, " not-%s(L%d)", L.diff_dir[i] == XM_DIR_OUT ? "out" : "in", L.diff_level[i]);
+            s += buf;
+        }
+        s += "\n";
     }
     return s;
 }

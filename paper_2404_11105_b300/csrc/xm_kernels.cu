@@ -104,17 +104,28 @@ struct LvState {
     int32_t empty;
 };
 
+// Per-warp state in shared memory. Only the first k entries of st[] exist
+// (the layout is cut to the plan's size so that more of the SM's on-chip
+// memory stays L1 cache); never index st[] at or beyond k.
 struct WarpSmem {
-    LvState st[XM_MAXK];
     int32_t m[XM_MAXK];
+    LvState st[XM_MAXK];
 };
 
-__host__ __device__ size_t batch_warp_bytes_impl(int kmax, int window) {
-    return ((sizeof(XmPlanDev) + 15) & ~size_t(15)) + ((sizeof(WarpSmem) + 15) & ~size_t(15)) +
-           (size_t)(kmax > 2 ? kmax - 2 : 0) * window * sizeof(int32_t);
+__host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Bytes of a plan copy holding levels 0..k-1, and of a warp's state for k levels.
+__host__ __device__ constexpr size_t plan_bytes(int k) {
+    return al16(offsetof(XmPlanDev, lv) + (size_t)k * sizeof(XmLevel));
+}
+__host__ __device__ constexpr size_t warp_state_bytes(int k) {
+    return al16(offsetof(WarpSmem, st) + (size_t)k * sizeof(LvState));
 }
 
-__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ size_t batch_warp_bytes_impl(int kmax, int window) {
+    return plan_bytes(kmax) + warp_state_bytes(kmax) + (size_t)(kmax > 2 ? kmax - 2 : 0) * window * sizeof(int32_t);
+}
+
 
 __host__ __device__ constexpr int n_windows(int k) { return k > 3 ? k - 3 : 0; }
 
@@ -201,6 +212,20 @@ __device__ __forceinline__ bool passes_degree(const GraphDev& g, int32_t x, int 
     return true;
 }
 
+__device__ __forceinline__ bool list_has(const ListRef& r, int32_t x) {
+    if (r.T) return hash_has(r.tab, r.T, x);
+    const int q = lbound(r.p, 0, r.len, x, false);
+    return q < r.len && __ldg(r.p + q) == x;
+}
+
+// Induced plans: x must lie in none of the level's difference lists. Kept out
+// of line so that plans without differences do not pay for its code.
+__device__ __noinline__ bool passes_diffs(const XmLevel& L, const GraphDev& g, const int32_t* m, int32_t x) {
+    for (int i = 0; i < L.ndiff; i++)
+        if (list_has(op_list(g, L.diff_dir[i], m[L.diff_level[i]]), x)) return false;
+    return true;
+}
+
 __device__ __forceinline__ int ceil_log2p1(int len) {  // ceil(log2(len + 1))
     return 32 - __clz(len);
 }
@@ -218,7 +243,8 @@ __device__ __forceinline__ int owner_of(const int32_t* __restrict__ prefix, int 
 // ------------------------------------------------ first-level candidate sets
 
 __device__ __forceinline__ void plan_to_smem(XmPlanDev& P, const XmPlanDev* __restrict__ plan_g) {
-    for (int i = threadIdx.x; i < (int)(sizeof(XmPlanDev) / 4); i += blockDim.x)
+    const int words = (int)(plan_bytes(__ldg(&plan_g->k)) / 4);
+    for (int i = threadIdx.x; i < words; i += blockDim.x)
         reinterpret_cast<int32_t*>(&P)[i] = reinterpret_cast<const int32_t*>(plan_g)[i];
     __syncthreads();
 }
@@ -299,6 +325,7 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
                 }
             }
             if (ok && filter_deg) ok = passes_degree(g, x, L1.dout_min, L1.din_min);
+            if (ok && L1.ndiff) ok = passes_diffs(L1, g, &v, x);
             const unsigned mask = __ballot_sync(FULL, ok);
             if (WRITE && ok) {
                 const int at = cnt + __popc(mask & ((1u << lane) - 1));
@@ -455,6 +482,7 @@ __device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, 
             for (uint32_t nm = L.neq_mask; nm; nm &= nm - 1)
                 if (x == ws.m[__ffs(nm) - 1]) ok = false;
         }
+        if (ok && L.ndiff) ok = passes_diffs(L, g, ws.m, x);
         if (WINDOW && ok) ok = passes_degree(g, x, L.dout_min, L.din_min);
         const unsigned mask = __ballot_sync(FULL, ok);
         const int rank = __popc(mask & ((1u << lane) - 1));
@@ -508,7 +536,7 @@ __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, 
     __syncwarp();
     if (MODE == MODE_STATS && lane == 0) leaf_elems += end - pos;
     const XmLevel& L = P.lv[l];
-    if (MODE != MODE_EMIT && S.nprobe == 0) {
+    if (MODE != MODE_EMIT && S.nprobe == 0 && L.ndiff == 0) {
         // A single list: its size, minus already matched nodes inside it.
         unsigned long long c = end - pos;
         for (uint32_t nm = L.neq_mask; nm; nm &= nm - 1) {
@@ -702,10 +730,10 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
     const int wib = threadIdx.x >> 5;
     const int k = P.k;
     const int W = ra.window;
-    const size_t warp_bytes = align16(sizeof(WarpSmem)) + (size_t)n_windows(k) * W * sizeof(int32_t);
-    unsigned char* wbase = smem + align16(sizeof(XmPlanDev)) + (size_t)wib * warp_bytes;
+    const size_t warp_bytes = warp_state_bytes(k) + (size_t)n_windows(k) * W * sizeof(int32_t);
+    unsigned char* wbase = smem + plan_bytes(k) + (size_t)wib * warp_bytes;
     WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase);
-    int32_t* wins = reinterpret_cast<int32_t*>(wbase + align16(sizeof(WarpSmem)));  // level l >= 2 at (l-2)*W
+    int32_t* wins = reinterpret_cast<int32_t*>(wbase + warp_state_bytes(k));  // level l >= 2 at (l-2)*W
     const GraphDev& g = ra.g;
     const bool two_level = !ra.l2_units;
     // unit index space: pieces of a start node's first-level set, or pieces
@@ -868,8 +896,8 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
     const size_t warp_bytes = batch_warp_bytes_impl(b.kmax, W);
     unsigned char* wbase = smem + (size_t)wib * warp_bytes;
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(wbase);
-    WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase + align16(sizeof(XmPlanDev)));
-    int32_t* wins = reinterpret_cast<int32_t*>(wbase + align16(sizeof(XmPlanDev)) + align16(sizeof(WarpSmem)));
+    WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase + plan_bytes(b.kmax));
+    int32_t* wins = reinterpret_cast<int32_t*>(wbase + plan_bytes(b.kmax) + warp_state_bytes(b.kmax));
     const long long total = __ldg(b.unit_prefix + b.npairs);
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     RunArgs ra{};  // count mode: no emission buffer
@@ -903,7 +931,7 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
                 cur = lo;
                 const int2 pg = b.pairs[cur];
                 __syncwarp();
-                for (int i = lane; i < (int)(sizeof(XmPlanDev) / 4); i += 32)
+                for (int i = lane; i < (int)(plan_bytes(__ldg(&b.plans[pg.x].k)) / 4); i += 32)
                     reinterpret_cast<int32_t*>(&P)[i] = reinterpret_cast<const int32_t*>(b.plans + pg.x)[i];
                 g = b.graphs[pg.y];
                 __syncwarp();
@@ -1037,8 +1065,8 @@ cudaError_t scan_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_
 size_t batch_warp_bytes(int kmax, int window) { return batch_warp_bytes_impl(kmax, window); }
 
 size_t match_smem_bytes(int k, int window, int warps) {
-    size_t warp_bytes = align16(sizeof(WarpSmem)) + (size_t)n_windows(k) * window * sizeof(int32_t);
-    return align16(sizeof(XmPlanDev)) + warp_bytes * warps;
+    size_t warp_bytes = warp_state_bytes(k) + (size_t)n_windows(k) * window * sizeof(int32_t);
+    return plan_bytes(k) + warp_bytes * warps;
 }
 
 int64_t chunk_capacity(int32_t n, int64_t m) { return (int64_t)n + (m + L1_CHUNK - 1) / L1_CHUNK; }
@@ -1069,7 +1097,7 @@ bool use_l2_units(const XmPlanDev& P) {
     // intersects lists (a single list is counted in O(log) per candidate)
     const XmLevel& L = P.lv[2];
     const int lists = (L.reuse >= 1 ? 1 : 0) + L.nops - (L.reuse >= 1 ? __builtin_popcount(L.reuse_ops) : 0);
-    return lists > 1;
+    return lists + L.ndiff > 1;
 }
 
 cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev, const RunArgs& a,

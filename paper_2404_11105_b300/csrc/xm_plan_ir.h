@@ -20,7 +20,10 @@
 //     by an operand list or an order bound);
 //   - degree: outdeg(x) >= dout_min and indeg(x) >= din_min (vertex
 //     constraint of Sec. 2; skipped at the last level, where it cannot
-//     prune).
+//     prune);
+//   - difference (induced plans only): x not in N_out(m_j) for each
+//     (diff_level, diff_dir = OUT) -- no pattern arc order[j] -> order[l] --
+//     and x not in N_in(m_j) for (j, IN) -- no arc order[l] -> order[j].
 #pragma once
 #include <stdint.h>
 
@@ -40,6 +43,9 @@ struct XmLevel {
     uint32_t lo_mask;
     uint32_t hi_mask;
     uint32_t neq_mask;
+    int32_t ndiff;
+    int32_t diff_level[XM_MAXOPS];
+    int32_t diff_dir[XM_MAXOPS];
 };
 
 struct XmPlanDev {

@@ -50,6 +50,8 @@ def run_plan(n, out, inn, plan, use_reuse=True):
                 continue
             if any(x == m[j] for j in range(l) if L["neq_mask"] >> j & 1):
                 continue
+            if any(x in (out[m[j]] if d == 0 else inn[m[j]]) for j, d in L.get("diffs", [])):
+                continue
             if not last and (len(out[x]) < L["dout_min"] or len(inn[x]) < L["din_min"]):
                 continue
             res.add(x)

@@ -148,3 +148,23 @@ def test_plan_semantics_vs_oracle(seed, pattern):
         assert run_plan(n, out, inn, p, use_reuse=False) == want
     pe = xm.Plan(pattern, xm.XM_EMBEDDINGS)
     assert run_plan(n, out, inn, pe) == want_emb
+
+
+@pytest.mark.parametrize("pattern", NAMED + list(synth.MOTIFS3.values()) + random_patterns(8, 17))
+def test_induced_plans_vs_oracle(pattern):
+    k, arcs = pattern
+    aset = set(arcs)
+    n, src, dst = synth.er_graph(10, 40, seed=8)
+    out, inn = adjacency_lists(n, src, dst)
+    g = oracle.OracleGraph(n, src, dst)
+    for flags in (xm.XM_INDUCED, xm.XM_INDUCED | xm.XM_NO_REDUCE):
+        p = xm.Plan(pattern, flags)
+        order = p.order()
+        for l in range(k):
+            v = order[l]
+            want = sorted([(j, 0) for j in range(l) if (order[j], v) not in aset] +
+                          [(j, 1) for j in range(l) if (v, order[j]) not in aset])
+            assert sorted(p.level(l)["diffs"]) == want
+        assert run_plan(n, out, inn, p) == g.count_matches(pattern, induced=True)
+    pe = xm.Plan(pattern, xm.XM_INDUCED | xm.XM_EMBEDDINGS)
+    assert run_plan(n, out, inn, pe) == g.count_embeddings(pattern, induced=True)
