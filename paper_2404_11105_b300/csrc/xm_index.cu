@@ -1,6 +1,6 @@
-// Hash index of the adjacency lists: one open-addressing table per list of
-// at least HASH_MIN_LEN ids, so that membership tests against long lists
-// (the probes of a candidate-set intersection) take about one memory access
+// Hash index of the adjacency lists: one bucketed open-addressing table per
+// list of at least HASH_MIN_LEN ids, so that a membership test against a long
+// list (a probe of a candidate-set intersection) is one 32-byte sector read
 // instead of a binary search.
 #include "xm_kernels.cuh"
 
@@ -8,7 +8,8 @@ namespace xm {
 
 namespace {
 
-// One warp per list; lanes insert the list's ids with atomicCAS.
+// One warp per list; lanes insert the list's ids with atomicCAS into the
+// first free slot of their bucket (or of the following buckets).
 __global__ void k_hash_build(const int32_t* __restrict__ off, const int32_t* __restrict__ adj,
                              const int64_t* __restrict__ hoff, int32_t* __restrict__ htab, int32_t n) {
     const int lane = threadIdx.x & 31;
@@ -17,15 +18,19 @@ __global__ void k_hash_build(const int32_t* __restrict__ off, const int32_t* __r
         const int64_t t0 = hoff[v];
         const uint32_t T = (uint32_t)(hoff[v + 1] - t0);
         if (T == 0) continue;
+        const uint32_t nb = T / HASH_BUCKET;
         int32_t* tab = htab + t0;
         for (int i = off[v] + lane; i < off[v + 1]; i += 32) {
             const int32_t x = adj[i];
-            uint32_t h = hash_slot(x, T);
-            // a table is at most half full, so an empty slot is always found
-            for (uint32_t probe = 0; probe < T; probe++) {
-                const int32_t old = atomicCAS(tab + h, -1, x);
-                if (old == -1 || old == x) break;
-                h = (h + 1) & (T - 1);
+            uint32_t b = hash_bucket(x, nb);
+            // a table is at most half full, so a free slot is always found
+            bool placed = false;
+            for (uint32_t step = 0; step < nb && !placed; step++) {
+                for (int s = 0; s < HASH_BUCKET; s++) {
+                    const int32_t old = atomicCAS(tab + (size_t)b * HASH_BUCKET + s, -1, x);
+                    if (old == -1 || old == x) { placed = true; break; }
+                }
+                b = (b + 1) & (nb - 1);
             }
         }
     }

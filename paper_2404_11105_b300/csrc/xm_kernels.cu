@@ -158,16 +158,21 @@ __device__ __forceinline__ ListRef op_list(const GraphDev& g, int dir, int32_t v
     return r;
 }
 
-// Is x in the list whose hash table is tab[0..T)? (linear probing; a table
-// is at most half full, so the scan stops at an empty slot)
+// Is x in the list whose hash table is tab[0..T)? Each bucket is one
+// 32-byte sector read as two 16-byte vectors; a bucket with an empty slot
+// ends the search (tables are at most half full).
 __device__ __forceinline__ bool hash_has(const int32_t* __restrict__ tab, uint32_t T, int32_t x) {
-    uint32_t h = hash_slot(x, T);
-    for (;;) {
-        const int32_t y = __ldg(tab + h);
-        if (y == x) return true;
-        if (y < 0) return false;
-        h = (h + 1) & (T - 1);
+    const uint32_t nb = T / HASH_BUCKET;
+    uint32_t b = hash_bucket(x, nb);
+    for (uint32_t step = 0; step < nb; step++) {
+        const int4* q = reinterpret_cast<const int4*>(tab + (size_t)b * HASH_BUCKET);
+        const int4 a = __ldg(q), c = __ldg(q + 1);
+        if (a.x == x || a.y == x || a.z == x || a.w == x || c.x == x || c.y == x || c.z == x || c.w == x)
+            return true;
+        if ((a.x | a.y | a.z | a.w | c.x | c.y | c.z | c.w) < 0) return false;  // an empty slot (-1)
+        b = (b + 1) & (nb - 1);
     }
+    return false;
 }
 
 // Order bounds of a level: candidates x must satisfy lo < x < hi.

@@ -26,21 +26,27 @@ struct GraphDev {
 constexpr int HASH_MIN_LEN = 32;
 
 // Multiplicative (Fibonacci) hashing, Knuth TAOCP vol. 3 sec. 6.4: the top
-// log2(T) bits of x * 2654435769 mod 2^32 select the first slot; collisions
-// probe the following slots (linear probing, wrapping).
-__host__ __device__ __forceinline__ uint32_t hash_slot(int32_t x, uint32_t T) {
+// log2(B) bits of x * 2654435769 mod 2^32 select the first bucket of a table
+// of B buckets of HASH_BUCKET slots (one 32-byte sector); a full bucket
+// continues in the next one (linear probing over buckets, wrapping). Slots
+// fill in order within a bucket, so a bucket holding an empty slot (-1)
+// ends a search.
+constexpr int HASH_BUCKET = 8;
+
+__host__ __device__ __forceinline__ uint32_t hash_bucket(int32_t x, uint32_t nbuckets) {
 #ifdef __CUDA_ARCH__
-    const int b = __ffs((int)T) - 1;
+    const int b = __ffs((int)nbuckets) - 1;
 #else
-    const int b = __builtin_ctz(T);
+    const int b = __builtin_ctz(nbuckets);
 #endif
-    return ((uint32_t)x * 2654435769u) >> (32 - b);
+    return b ? (((uint32_t)x * 2654435769u) >> (32 - b)) : 0u;
 }
 
-// Table size for a list of `len` ids (0: no table).
+// Table size in slots for a list of `len` ids (0: no table): a power of two
+// at least twice the length, so tables are at most half full.
 inline uint32_t hash_table_size(int64_t len) {
     if (len < HASH_MIN_LEN) return 0;
-    uint32_t t = 1;
+    uint32_t t = HASH_BUCKET;
     while ((int64_t)t < 2 * len) t <<= 1;
     return t;
 }
