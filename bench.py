@@ -438,6 +438,7 @@ def main():
     ap.add_argument("--root-sample", type=int, default=1024,
                     help="rmat24: count over a seeded uniform sample of 1/N of the start nodes")
     ap.add_argument("--budget-ms", type=int, default=0, help="device-time budget per count call (0: none)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the per-pattern autotuner (warm-up phase)")
     ap.add_argument("--ablation", action="store_true",
                     help="also time every pattern with its unreduced plan (no candidate-set reuse)")
     ap.add_argument("--enum-capacity", type=int, default=1 << 24,
@@ -498,6 +499,15 @@ def main():
             counts = allreduce_counts(counts, dist, device="cuda")
         return counts
 
+    tuned = {}
+    if not args.no_tune:
+        # project autotuner (untimed, part of warm-up): window, warps per
+        # block and unit size per pattern on this graph
+        cands = [(w, u, wpb, 0, args.budget_ms) for w in (256, 512) for wpb in (4, 8, 16) for u in (8, 32)]
+        for name, p in plans.items():
+            if roots is None and world == 1:
+                best, _ = xm.xm_plan_tune(g, p, cands, reps=1)
+                tuned[name] = {k: best[k] for k in ("window", "unit", "warps_per_block")}
     for _ in range(args.warmup):
         counts = step()
 
@@ -637,6 +647,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": LAUNCHES_PER_CALL * launches, "clocks": clocks,
             "counts": {k: int(v) for k, v in counts.items()}, "enumeration": enum, "ablation": ablation,
+            "autotuned": tuned,
             "device_ms_per_pattern": {k: round(statistics.median(v), 3) for k, v in per_pattern_ms.items()}}
     print(json.dumps(line), flush=True)
     if world > 1:

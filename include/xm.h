@@ -232,6 +232,16 @@ int xm_plan_set_tuning(xm_plan p, const xm_tuning *t);
 /* Reads back the effective tuning. */
 int xm_plan_get_tuning(xm_plan p, xm_tuning *t);
 
+/*
+ * xm_plan_tune -- autotuner for one (plan, graph) pair: runs xm_count once
+ * per candidate to warm up, then `reps` times, timed with the graph's CUDA
+ * events (xm_graph_last_timing); keeps the fastest candidate as the plan's
+ * tuning and reports it. Every candidate must give the same count (else
+ * XM_EINVAL). Synchronises `stream`.
+ */
+int xm_plan_tune(xm_graph g, xm_plan p, const xm_tuning *cand, int32_t ncand, int32_t reps, xm_tuning *best,
+                 float *best_ms, void *stream);
+
 /* ------------------------------------------------------------ matching */
 
 /*

@@ -29,7 +29,7 @@ EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_gr
            "xm_count_noalloc", "xm_batch_create", "xm_batch_set_tuning", "xm_batch_get_tuning", "xm_batch_run",
            "xm_batch_run_graph", "xm_batch_counts", "xm_batch_tune", "xm_batch_free", "xm_count_batch",
            "xm_query_bytes", "xm_server_create", "xm_server_submit", "xm_server_poll", "xm_server_info",
-           "xm_server_free", "xm_count_roots", "xm_enumerate_roots", "xm_count_roots_stats"]
+           "xm_server_free", "xm_count_roots", "xm_enumerate_roots", "xm_count_roots_stats", "xm_plan_tune"]
 
 
 class XmError(RuntimeError):
@@ -98,6 +98,8 @@ def _load():
         "xm_count_batch": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64, i32p, u64p, vp]),
         "xm_query_bytes": (ctypes.c_uint64, [vp, vp]),
         "xm_count_roots": (ctypes.c_int, [vp, vp, i32p, i64, u64p, u64p, vp]),
+        "xm_plan_tune": (ctypes.c_int, [vp, vp, ctypes.POINTER(xm_tuning), i32, i32, ctypes.POINTER(xm_tuning),
+                                        ctypes.POINTER(ctypes.c_float), vp]),
         "xm_count_roots_stats": (ctypes.c_int, [vp, vp, i32p, i64, u64p, u64p, ctypes.POINTER(xm_stats), vp]),
         "xm_enumerate_roots": (ctypes.c_int, [vp, vp, i32p, i64, vp, ctypes.c_uint64, u64p, u64p, vp]),
         "xm_server_create": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.c_uint64, ctypes.POINTER(vp)]),
@@ -433,3 +435,13 @@ def xm_count_roots_stats(g: Graph, p: Plan, roots, stream=None):
     _check(lib().xm_count_roots_stats(g._h, p._h, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(r),
                                       ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(st), _stream(stream)))
     return (hi.value << 64) | lo.value, {f: getattr(st, f) for f, _ in xm_stats._fields_ if f != "reserved"}
+
+
+def xm_plan_tune(g: Graph, p: Plan, candidates, reps: int = 2, stream=None):
+    """Autotune p's launch parameters on graph g; returns (best tuning, ms)."""
+    arr = (xm_tuning * len(candidates))(*[xm_tuning(*c) for c in candidates])
+    best = xm_tuning()
+    ms = ctypes.c_float()
+    _check(lib().xm_plan_tune(g._h, p._h, arr, len(candidates), reps, ctypes.byref(best), ctypes.byref(ms),
+                              _stream(stream)))
+    return {f: getattr(best, f) for f, _ in xm_tuning._fields_}, ms.value

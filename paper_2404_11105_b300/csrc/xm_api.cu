@@ -388,6 +388,42 @@ int xm_plan_get_tuning(xm_plan p, xm_tuning* t) {
     return XM_OK;
 }
 
+int xm_plan_tune(xm_graph g, xm_plan p, const xm_tuning* cand, int32_t ncand, int32_t reps, xm_tuning* best,
+                 float* best_ms, void* stream) {
+    if (!g || !p || !cand || ncand < 1 || reps < 1) { set_error("bad tuning arguments"); return XM_EINVAL; }
+    const xm_tuning keep = p->tuning;
+    float best_t = -1.0f;
+    xm_tuning best_c = keep;
+    uint64_t want_lo = 0, want_hi = 0;
+    for (int c = 0; c < ncand; c++) {
+        int rc = xm_plan_set_tuning(p, &cand[c]);
+        if (rc) { p->tuning = keep; return rc; }
+        float t_min = -1.0f;
+        for (int r = 0; r <= reps; r++) {  // the first run warms up
+            uint64_t lo = 0, hi = 0;
+            rc = xm_count(g, p, &lo, &hi, stream);
+            if (rc) { p->tuning = keep; return rc; }
+            if (c == 0 && r == 0) { want_lo = lo; want_hi = hi; }
+            if (lo != want_lo || hi != want_hi) {
+                p->tuning = keep;
+                set_error("tunings disagree on the count");
+                return XM_EINVAL;
+            }
+            float a = 0, b = 0;
+            if ((rc = xm_graph_last_timing(g, &a, &b))) { p->tuning = keep; return rc; }
+            if (r > 0 && (t_min < 0 || a + b < t_min)) t_min = a + b;
+        }
+        if (best_t < 0 || t_min < best_t) {
+            best_t = t_min;
+            best_c = p->tuning;
+        }
+    }
+    p->tuning = best_c;
+    if (best) *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return XM_OK;
+}
+
 int xm_count(xm_graph g, xm_plan p, uint64_t* lo, uint64_t* hi, void* stream) {
     return run(g, p, MODE_COUNT, 0, INT32_MAX, nullptr, 0, lo, hi, nullptr, nullptr, (cudaStream_t)stream);
 }

@@ -353,3 +353,14 @@ def test_induced_motif_census_s20(xm, s20):
             v = int(v)
             assert xm.xm_count_range(g, pe, v, v + 1) == og.count_embeddings(synth.MOTIFS3[nm], pe.start, v, v + 1,
                                                                              induced=True)
+
+
+def test_plan_autotuner(xm, rmat_small):
+    g, og = rmat_small
+    p = xm.Plan(synth.BIFAN)
+    want = og.count_matches(synth.BIFAN)
+    cands = [(64, 1, 2, 0, 0), (256, 8, 8, 0, 0), (512, 32, 4, 1, 0)]
+    best, ms = xm.xm_plan_tune(g, p, cands, reps=2)
+    assert ms > 0 and tuple(best.values()) in cands
+    assert p.tuning() == best
+    assert xm.xm_count(g, p) == want
