@@ -323,8 +323,8 @@ def run_batch(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     G, P = args.batch_graphs, args.batch_patterns
     t0 = time.perf_counter()
-    graphs = [xm.Graph(*synth.small_graph(i, seed=5)) for i in range(G)]
-    pats = [synth.batch_pattern(i, seed=4) for i in range(P)]
+    graphs = [xm.Graph(*synth.small_graph(i, seed=5, n_hi=args.batch_nmax)) for i in range(G)]
+    pats = [synth.batch_pattern(i, seed=4, k_hi=args.batch_kmax) for i in range(P)]
     plans = [xm.Plan(p) for p in pats]
     load_s = time.perf_counter() - t0
     pairs = [(pi, gi) for pi in range(P) for gi in range(G)]
@@ -395,9 +395,9 @@ def run_batch(args):
     line = {"metric": "patterns/s", "value": npairs / (ms / 1000.0), "unit": "(pattern, graph) pairs/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"{P} random connected patterns (k 3-6, density 0.3-0.7, seed 4) x {G} small "
-                                   f"graphs (n log-uniform 50-5000, mean out-degree 4-12, ER/R-MAT alternating, "
-                                   f"seed 5)", "pairs": npairs, "matches_per_step": total,
+            "config": {"workload": f"{P} random connected patterns (k 3-{args.batch_kmax}, density 0.3-0.7, seed 4) "
+                                   f"x {G} small graphs (n log-uniform 50-{args.batch_nmax}, mean out-degree 4-12, "
+                                   f"ER/R-MAT alternating, seed 5)", "pairs": npairs, "matches_per_step": total,
                        "graph_load_s": round(load_s, 1), "autotuned": best,
                        "autotune_sub_batch_ms": round(best_ms, 3)},
             "matches_per_s": total / (ms / 1000.0),
@@ -427,6 +427,8 @@ def main():
     ap.add_argument("--serve-kmax", type=int, default=6)
     ap.add_argument("--batch-graphs", type=int, default=10000)
     ap.add_argument("--batch-patterns", type=int, default=256)
+    ap.add_argument("--batch-kmax", type=int, default=6, help="largest pattern (vertices) in the batch")
+    ap.add_argument("--batch-nmax", type=int, default=5000, help="largest graph (nodes) in the batch")
     ap.add_argument("--batch-single-sample", type=int, default=400,
                     help="pairs timed one xm_count call at a time (extrapolated)")
     ap.add_argument("--e2e-steps", type=int, default=2)
