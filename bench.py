@@ -46,6 +46,10 @@ def workload(name):
         n, src, dst = synth.rmat24()
         pats = dict(synth.S24_PATTERNS)
         desc = "R-MAT scale 24 EF16 a=.57 b=.19 c=.19 seed 3; 4-cycle, bi-fan, bi-parallel, 5-vertex FF chain"
+    elif name == "rmat22":
+        n, src, dst = synth.rmat_graph(22, 16, seed=6)
+        pats = dict(synth.S24_PATTERNS)
+        desc = "R-MAT scale 22 EF16 a=.57 b=.19 c=.19 seed 6; 4-cycle, bi-fan, bi-parallel, 5-vertex FF chain"
     else:
         n, src, dst = synth.rmat20()
         pats = dict(synth.MOTIFS3)
@@ -418,7 +422,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="xm", choices=["xm", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rmat24", "batch", "serve"])
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rmat22", "rmat24", "batch", "serve"])
     ap.add_argument("--serve-graphs", type=int, default=1000)
     ap.add_argument("--serve-rates", default="100,300,1000,3000,10000")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate")
@@ -476,7 +480,7 @@ def main():
             p.set_tuning(budget_ms=args.budget_ms)
     r_lo, r_hi = shard_bounds(n, src, dst, world)[rank]
     roots = None
-    if args.workload == "rmat24":
+    if args.workload in ("rmat22", "rmat24"):
         # a seeded uniform sample of the start nodes (the paper's percentage-
         # of-start-nodes runs); a full scale-24 count of these patterns is
         # far beyond a one-minute step

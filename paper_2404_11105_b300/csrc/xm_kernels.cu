@@ -175,6 +175,17 @@ __device__ __forceinline__ bool hash_has(const int32_t* __restrict__ tab, uint32
     return false;
 }
 
+// First bucket of a probe, split from the rest so that several probes can be
+// in flight at once: sets `found`, and returns true when the first bucket
+// settles the answer (x found, or an empty slot seen).
+__device__ __forceinline__ bool hash_first(const int32_t* __restrict__ tab, uint32_t T, int32_t x, bool& found) {
+    const uint32_t b = hash_bucket(x, T / HASH_BUCKET);
+    const int4* q = reinterpret_cast<const int4*>(tab + (size_t)b * HASH_BUCKET);
+    const int4 a = __ldg(q), c = __ldg(q + 1);
+    found = a.x == x || a.y == x || a.z == x || a.w == x || c.x == x || c.y == x || c.z == x || c.w == x;
+    return found || (a.x | a.y | a.z | a.w | c.x | c.y | c.z | c.w) < 0;
+}
+
 // Order bounds of a level: candidates x must satisfy lo < x < hi.
 __device__ __forceinline__ void level_bounds(const XmLevel& L, const int32_t* m, int32_t& lo, int32_t& hi) {
     lo = -1;
@@ -522,6 +533,40 @@ __device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, 
     return leaf;
 }
 
+// Last-level count when every probe list has a hash table: 64 driver ids
+// per iteration (two per lane) with the first-bucket probes of both issued
+// before either is checked, so twice as many sector reads are in flight.
+__device__ unsigned long long leaf_count_hashed(const XmLevel& L, WarpSmem& ws, LvState& S, int lane) {
+    const bool dsh = S.drv_shared;
+    const int np = S.nprobe;
+    const int end = S.drv_end;
+    unsigned long long cnt = 0;
+    for (int pos = S.drv_pos; pos < end; pos += 64) {
+        const int i0 = pos + lane, i1 = pos + 32 + lane;
+        const bool v0 = i0 < end, v1 = i1 < end;
+        const int32_t x0 = v0 ? ld(S.drv, i0, dsh) : 0;
+        const int32_t x1 = v1 ? ld(S.drv, i1, dsh) : 0;
+        bool ok0 = v0, ok1 = v1;
+        for (int p = 0; p < np; p++) {
+            const int32_t* tab = S.ptab[p];
+            const uint32_t T = S.pT[p];
+            bool f0 = false, f1 = false;
+            const bool d0 = ok0 ? hash_first(tab, T, x0, f0) : true;
+            const bool d1 = ok1 ? hash_first(tab, T, x1, f1) : true;
+            if (ok0) ok0 = d0 ? f0 : hash_has(tab, T, x0);
+            if (ok1) ok1 = d1 ? f1 : hash_has(tab, T, x1);
+            if (__ballot_sync(FULL, ok0 || ok1) == 0) break;
+        }
+        for (uint32_t nm = L.neq_mask; nm; nm &= nm - 1) {
+            const int32_t y = ws.m[__ffs(nm) - 1];
+            ok0 = ok0 && x0 != y;
+            ok1 = ok1 && x1 != y;
+        }
+        cnt += __popc(__ballot_sync(FULL, ok0)) + __popc(__ballot_sync(FULL, ok1));
+    }
+    return lane == 0 ? cnt : 0;
+}
+
 // Count (or emit) the candidates of the last level l >= 2.
 template <int MODE>
 __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane,
@@ -550,6 +595,11 @@ __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, 
             if (q < end && ld(S.drv, q, S.drv_shared) == y) c--;
         }
         return lane == 0 ? c : 0;
+    }
+    if (MODE == MODE_COUNT && L.ndiff == 0) {
+        bool hashed = S.probe_shared == 0;
+        for (int p = 0; p < S.nprobe && hashed; p++) hashed = S.pT[p] != 0;
+        if (hashed) return leaf_count_hashed(L, ws, S, lane);
     }
     unsigned long long r = scan_level<MODE, false>(P, g, ws, S, l, nullptr, 0, lane, ra, stat_bytes);
     return lane == 0 ? r : 0;
