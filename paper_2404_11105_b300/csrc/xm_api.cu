@@ -95,6 +95,7 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
     a.e_units = g->d_e_units;
     a.emax = (int32_t)std::max<int64_t>(g->m, 1);
     a.l2_units = use_l2_units(P.dev) ? 1 : 0;
+    a.leaf_kind = a.l2_units ? 0 : leaf_closed_form_kind(P.dev);
     a.block_sums = g->d_block_sums;
     a.n_block_sums = g->n_block_sums;
     a.ctl = g->d_ctl;

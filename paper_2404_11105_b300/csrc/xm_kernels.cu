@@ -775,6 +775,55 @@ __global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     }
 }
 
+// Three-vertex plans whose last level needs no intersection per partial
+// match (leaf_kind, chosen on the host by leaf_closed_form_kind):
+//   1: the last level's candidates are the first level's set itself (reuse
+//      of all its operands): the count for the candidate at index i follows
+//      from i and the set's cut by the start node's bounds;
+//   2: the last level is one list of the start node: its cut length, minus
+//      the first-level node when injectivity demands and it lies inside.
+// One lane per first-level candidate of the unit [a, b); returns the lane's
+// count.
+__device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDev& g, int kind, int32_t m0,
+                                               const int32_t* set, int set_len, int a, int b, int lane) {
+    const XmLevel& L = P.lv[2];
+    const int32_t lo0 = (L.lo_mask & 1u) ? m0 : -1;
+    const int32_t hi0 = (L.hi_mask & 1u) ? m0 : INT_MAX;
+    const int32_t* list = set;
+    int len = set_len;
+    if (kind == 2) {
+        const ListRef r = op_list(g, L.op_dir[0], m0);
+        list = r.p;
+        len = r.len;
+    }
+    const int c0 = lo0 >= 0 ? lbound(list, 0, len, lo0 + 1, false) : 0;
+    const int c1 = hi0 != INT_MAX ? lbound(list, c0, len, hi0, false) : len;
+    unsigned long long acc = 0;
+    for (int i = a + lane; i < b; i += 32) {
+        const int32_t m1 = __ldg(set + i);
+        int lo = c0, hi = c1;
+        if (kind == 1) {
+            // positions in the set are the candidates' own indices
+            if (L.lo_mask & 2u) lo = max(lo, i + 1);
+            if (L.hi_mask & 2u) hi = min(hi, i);
+            long long c = hi > lo ? hi - lo : 0;
+            if ((L.neq_mask & 2u) && i >= lo && i < hi) c--;
+            acc += c;
+        } else {
+            if (L.lo_mask & 2u) lo = max(lo, lbound(list, lo, hi, m1 + 1, false));
+            if (L.hi_mask & 2u) hi = min(hi, lbound(list, lo, hi, m1, false));
+            long long c = hi > lo ? hi - lo : 0;
+            if ((L.neq_mask & 2u) && c > 0) {
+                // the first-level node itself is not a candidate
+                const int q = lbound(list, lo, hi, m1, false);
+                if (q < hi && __ldg(list + q) == m1) c--;
+            }
+            acc += c;
+        }
+    }
+    return acc;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -833,6 +882,10 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                 const int a = chunk * ra.unit;
                 const int b = min(s1 - s0, a + ra.unit);
                 if (MODE == MODE_STATS && lane == 0) st.bytes += 4ull * (b - a);
+                if (MODE == MODE_COUNT && ra.leaf_kind) {
+                    acc += leaf_closed_form(P, g, ra.leaf_kind, root_node(ra, root), base, s1 - s0, a, b, lane);
+                    continue;
+                }
                 if (lane == 0) {
                     ws.m[0] = root_node(ra, root);
                     LvState& S1 = ws.st[1];
@@ -1143,6 +1196,16 @@ cudaError_t launch_batch(const BatchDev& b, int warps_per_block, int blocks_per_
     const int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, occ) : occ;
     k_match_batch<<<nsm * bps, warps_per_block * 32, smem, stream>>>(b);
     return cudaGetLastError();
+}
+
+int leaf_closed_form_kind(const XmPlanDev& P) {
+    if (P.k != 3) return 0;
+    const XmLevel& L = P.lv[2];
+    if (L.ndiff) return 0;
+    if ((L.lo_mask | L.hi_mask | L.neq_mask) & ~3u) return 0;
+    if (L.reuse == 1 && __builtin_popcount(L.reuse_ops) == L.nops) return 1;
+    if (L.reuse < 1 && L.nops == 1 && L.op_level[0] == 0) return 2;
+    return 0;
 }
 
 bool use_l2_units(const XmPlanDev& P) {

@@ -77,6 +77,7 @@ struct RunArgs {
     int32_t* e_units;           // emax + 1: work units per first-level candidate, scanned
     int32_t emax;               // capacity of l1set / l1root (>= any number of first-level candidates)
     int32_t l2_units;           // 1: work units per first-level candidate; 0: per start node
+    int32_t leaf_kind;          // three-vertex plans: closed-form last level (leaf_closed_form_kind)
     int64_t* block_sums;        // scan partials
     int64_t n_block_sums;
     unsigned long long* ctl;    // control block
@@ -131,6 +132,9 @@ size_t match_smem_bytes(int k, int window, int warps);
 
 // Whether a plan's work units split below the first level (RunArgs::l2_units).
 bool use_l2_units(const XmPlanDev& P);
+// 0, or the closed form that counts a three-vertex plan's last level
+// without an intersection per partial match (RunArgs::leaf_kind).
+int leaf_closed_form_kind(const XmPlanDev& P);
 
 // Enqueues the whole matching pass on `stream`: first-level sets, work
 // units, persistent matcher. `plan_dev` is a device copy of the plan.
