@@ -434,6 +434,17 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
             Rl.din_min = std::min(Rl.din_min, L.din_min);
         }
     }
+    // A candidate drawn from the out-lists of `nout` earlier matched nodes
+    // (distinct by injectivity) has at least nout in-arcs, and likewise for
+    // in-lists: thresholds those lists already guarantee are dropped, so
+    // the kernels only gather degrees that can still prune.
+    for (int l = 1; l < k; l++) {
+        XmLevel& L = D.lv[l];
+        int nout = 0, nin = 0;
+        for (int i = 0; i < L.nops; i++) (L.op_dir[i] == XM_DIR_OUT ? nout : nin)++;
+        if (L.din_min <= nout) L.din_min = 0;
+        if (L.dout_min <= nin) L.dout_min = 0;
+    }
 
     out.dev = D;
     out.k = k;

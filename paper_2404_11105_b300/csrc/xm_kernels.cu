@@ -304,22 +304,53 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
     const bool filter_deg = P.k > 2;
     const XmLevel& L1 = P.lv[1];
     unsigned long long st_bytes = 0;
-    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c <= ra.cmax; c += nwarps) {
-        if (c >= total) {
-            if (!WRITE && lane == 0) ra.chunk_cnt[c] = 0;
-            continue;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // chunks past the last real one get a zero count
+    if (!WRITE)
+        for (int c = total + wid * 32 + lane; c <= ra.cmax; c += nwarps * 32) ra.chunk_cnt[c] = 0;
+    // warps take runs of consecutive chunks from a counter: a start node's
+    // lists are fetched once per run, and the chunks of a hub still spread
+    // over many warps
+    constexpr int RUN = 4;
+    unsigned long long* head = ra.ctl + CTL_L1_HEAD + (WRITE ? 1 : 0);
+    int vi = -1, v = 0, no = 0, c0 = 0, c1 = 0;
+    ListRef d{nullptr, 0, 0, nullptr, 0}, o{nullptr, 0, 0, nullptr, 0};
+    for (;;) {
+        int cb = 0;
+        if (lane == 0) cb = (int)min((unsigned long long)total, atomicAdd(head, (unsigned long long)RUN));
+        cb = __shfl_sync(FULL, cb, 0);
+        if (cb >= total) break;
+        const int ce = min(total, cb + RUN);
+    for (int c = cb; c < ce; c++) {
+        if (vi < 0 || c >= __ldg(ra.root_chunks + vi + 1)) {
+            if (vi >= 0 && c < __ldg(ra.root_chunks + min(vi + 8, ni))) {
+                do { vi++; } while (c >= __ldg(ra.root_chunks + vi + 1));
+            } else {
+                vi = owner_of(ra.root_chunks, ni, c);
+            }
+            v = root_node(ra, vi);
+            first_level_lists(P, g, v, d, o, no, c0, c1);
         }
-        const int vi = owner_of(ra.root_chunks, ni, c);
-        const int v = root_node(ra, vi);
         const int j = c - __ldg(ra.root_chunks + vi);
-        ListRef d, o;
-        int no, c0, c1;
-        first_level_lists(P, g, v, d, o, no, c0, c1);
         int pos = c0 + j * L1_CHUNK;
         const int end = min(c1, pos + L1_CHUNK);
         int plo = 0;
         int cnt = 0;
         int32_t* out = WRITE ? ra.l1set + ra.chunk_cnt[c] : nullptr;
+        const bool filtered = no || L1.ndiff || (filter_deg && (L1.dout_min > 0 || L1.din_min > 0));
+        if (!filtered && MODE != MODE_STATS) {
+            // every driver id survives: count without reading, or copy
+            if (WRITE) {
+                int32_t* own = ra.l1root + (out - ra.l1set);
+                for (int i = pos + lane; i < end; i += 32) {
+                    out[i - pos] = __ldg(d.p + i);
+                    own[i - pos] = vi;
+                }
+            } else if (lane == 0) {
+                ra.chunk_cnt[c] = end - pos;
+            }
+            continue;
+        }
         if (MODE == MODE_STATS && !WRITE && lane == 0) {
             const int run = end - pos;
             st_bytes += (j == 0 ? 8ull * (1 + no) : 0) + 4ull * run;
@@ -351,6 +382,7 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
             cnt += __popc(mask);
         }
         if (!WRITE && lane == 0) ra.chunk_cnt[c] = cnt;
+    }
     }
     if (MODE == MODE_STATS && !WRITE && lane == 0 && st_bytes) atomicAdd(ra.ctl + CTL_STATS + 0, st_bytes);
 }

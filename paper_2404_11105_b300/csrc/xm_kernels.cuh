@@ -63,6 +63,7 @@ enum {
     CTL_EMIT = 3,      // enumeration cursor
     CTL_STATUS = 4,    // error bits (1: unit count overflow, 2: time budget exceeded)
     CTL_T0 = 5,        // global-timer start of the matcher (budget reference)
+    CTL_L1_HEAD = 6,   // next first-level chunk (count pass); 7: write pass
     CTL_STATS = 8,     // 8 stats words (xm_stats order)
     CTL_WORDS = 16
 };
