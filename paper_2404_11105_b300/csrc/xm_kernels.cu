@@ -565,36 +565,41 @@ __device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, 
     return leaf;
 }
 
-// Last-level count when every probe list has a hash table: 64 driver ids
-// per iteration (two per lane) with the first-bucket probes of both issued
-// before either is checked, so twice as many sector reads are in flight.
+// Last-level count when every probe list has a hash table: 128 driver ids
+// per iteration (four per lane) with all four first-bucket probes issued
+// before any is checked, so four sector reads per lane are in flight.
 __device__ unsigned long long leaf_count_hashed(const XmLevel& L, WarpSmem& ws, LvState& S, int lane) {
     const bool dsh = S.drv_shared;
     const int np = S.nprobe;
     const int end = S.drv_end;
     unsigned long long cnt = 0;
-    for (int pos = S.drv_pos; pos < end; pos += 64) {
-        const int i0 = pos + lane, i1 = pos + 32 + lane;
-        const bool v0 = i0 < end, v1 = i1 < end;
-        const int32_t x0 = v0 ? ld(S.drv, i0, dsh) : 0;
-        const int32_t x1 = v1 ? ld(S.drv, i1, dsh) : 0;
-        bool ok0 = v0, ok1 = v1;
+    for (int pos = S.drv_pos; pos < end; pos += 128) {
+        int32_t x[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = pos + 32 * u + lane;
+            ok[u] = i < end;
+            x[u] = ok[u] ? ld(S.drv, i, dsh) : 0;
+        }
         for (int p = 0; p < np; p++) {
             const int32_t* tab = S.ptab[p];
             const uint32_t T = S.pT[p];
-            bool f0 = false, f1 = false;
-            const bool d0 = ok0 ? hash_first(tab, T, x0, f0) : true;
-            const bool d1 = ok1 ? hash_first(tab, T, x1, f1) : true;
-            if (ok0) ok0 = d0 ? f0 : hash_has(tab, T, x0);
-            if (ok1) ok1 = d1 ? f1 : hash_has(tab, T, x1);
-            if (__ballot_sync(FULL, ok0 || ok1) == 0) break;
+            bool f[4], dn[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) dn[u] = ok[u] ? hash_first(tab, T, x[u], f[u]) : (f[u] = false, true);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (ok[u]) ok[u] = dn[u] ? f[u] : hash_has(tab, T, x[u]);
+            if (__ballot_sync(FULL, ok[0] || ok[1] || ok[2] || ok[3]) == 0) break;
         }
         for (uint32_t nm = L.neq_mask; nm; nm &= nm - 1) {
             const int32_t y = ws.m[__ffs(nm) - 1];
-            ok0 = ok0 && x0 != y;
-            ok1 = ok1 && x1 != y;
+#pragma unroll
+            for (int u = 0; u < 4; u++) ok[u] = ok[u] && x[u] != y;
         }
-        cnt += __popc(__ballot_sync(FULL, ok0)) + __popc(__ballot_sync(FULL, ok1));
+#pragma unroll
+        for (int u = 0; u < 4; u++) cnt += __popc(__ballot_sync(FULL, ok[u]));
     }
     return lane == 0 ? cnt : 0;
 }
