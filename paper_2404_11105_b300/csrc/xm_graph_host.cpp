@@ -1,6 +1,12 @@
 // Host-side construction of the dual sorted CSR (out-lists and in-lists).
 // Graph loading is outside the timed matching work, as in the paper's
-// measurements (Sec. 6.1), so this is plain multi-threaded host code.
+// measurements (Sec. 6.1), but it is the whole of an end-to-end call's
+// host time, so it is a parallel bucket sort: arcs are scattered into
+// buckets of consecutive source ids (per-thread counts, one prefix sum), each
+// bucket is sorted as packed 64-bit (source, destination) keys and
+// deduplicated on its own, and the buckets are concatenated. The in-lists
+// are built the same way from the deduplicated arcs with the key halves
+// swapped.
 #include <algorithm>
 #include <atomic>
 #include <climits>
@@ -13,18 +19,131 @@ namespace xm {
 
 namespace {
 
+// one thread per 2^17 items, at most the hardware threads (and 64)
+int n_threads(int64_t work) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int64_t cap = std::min<int64_t>(hw ? hw : 1, 64);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(cap, work >> 17));
+}
+
 template <class F>
-void parallel_for(int64_t n, F f) {
-    unsigned hw = std::thread::hardware_concurrency();
-    int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 1, 64));
-    if (n < (1 << 16)) nt = 1;
-    if (nt == 1) { f(0, n); return; }
+void parallel_for(int64_t n, int nt, F f) {
+    if (nt <= 1 || n < 2) { f(0, 0, n); return; }
     std::vector<std::thread> th;
-    for (int64_t t = 0; t < nt; t++) {
+    for (int t = 0; t < nt; t++) {
         int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
-        th.emplace_back([=] { f(lo, hi); });
+        th.emplace_back([=] { f(t, lo, hi); });
     }
     for (auto& x : th) x.join();
+}
+
+// Sorted, repeat-free CSR of the keys (key_of(i) -> (row, col)) for rows
+// [0, n): off[n+1], adj[count]. Self-loops are dropped. Returns the number of
+// distinct arcs; above 2^31-1 nothing is filled (int32 offsets).
+template <class KeyOf>
+int64_t build_side(int32_t n, int64_t m, KeyOf key_of, HostVec<int32_t>& off, HostVec<int32_t>& adj) {
+    const int nt = n_threads(m);
+    // buckets of consecutive rows
+    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>({(int64_t)n, 8192, m >> 10}));
+    auto bucket = [&](uint32_t row) { return (int64_t)row * nb / n; };
+    std::vector<int64_t> cnt((size_t)nt * nb, 0);
+    parallel_for(m, nt, [&](int t, int64_t lo, int64_t hi) {
+        int64_t* c = cnt.data() + (size_t)t * nb;
+        for (int64_t i = lo; i < hi; i++) {
+            const uint64_t k = key_of(i);
+            const uint32_t r = (uint32_t)(k >> 32), col = (uint32_t)k;
+            if (r != col) c[bucket(r)]++;
+        }
+    });
+    // prefix over (bucket, thread)
+    std::vector<int64_t> start((size_t)nt * nb);
+    std::vector<int64_t> bstart(nb + 1, 0);
+    int64_t run = 0;
+    for (int64_t b = 0; b < nb; b++) {
+        bstart[b] = run;
+        for (int t = 0; t < nt; t++) {
+            start[(size_t)t * nb + b] = run;
+            run += cnt[(size_t)t * nb + b];
+        }
+    }
+    bstart[nb] = run;
+    HostVec<uint64_t> keys((size_t)std::max<int64_t>(run, 1));
+    parallel_for(m, nt, [&](int t, int64_t lo, int64_t hi) {
+        int64_t* s = start.data() + (size_t)t * nb;
+        for (int64_t i = lo; i < hi; i++) {
+            const uint64_t k = key_of(i);
+            const uint32_t r = (uint32_t)(k >> 32), col = (uint32_t)k;
+            if (r != col) keys[s[bucket(r)]++] = k;
+        }
+    });
+    // per bucket: counting sort of its keys by row into int32 columns, then
+    // sort + dedup each row; deg[r] = distinct columns of row r, compacted to
+    // the front of the row's slot
+    auto rows_of = [&](int64_t b, int64_t& lo, int64_t& hi) {
+        lo = (b * n + nb - 1) / nb;
+        hi = ((b + 1) * n + nb - 1) / nb;
+    };
+    HostVec<int32_t> cols((size_t)std::max<int64_t>(run, 1));
+    HostVec<int64_t> rstart((size_t)n);
+    HostVec<int32_t> deg((size_t)n);
+    std::vector<int64_t> kept(nb, 0);
+    std::atomic<int64_t> next{0};
+    auto sort_rows = [&](int, int64_t, int64_t) {
+        for (;;) {
+            const int64_t b = next.fetch_add(1);
+            if (b >= nb) break;
+            int64_t row_lo, row_hi;
+            rows_of(b, row_lo, row_hi);
+            const uint64_t* k = keys.data() + bstart[b];
+            const int64_t c = bstart[b + 1] - bstart[b];
+            const int64_t nr = row_hi - row_lo;
+            std::vector<int64_t> pos((size_t)nr + 1, 0);
+            for (int64_t i = 0; i < c; i++) pos[(int64_t)(k[i] >> 32) - row_lo + 1]++;
+            pos[0] = bstart[b];
+            for (int64_t r = 1; r <= nr; r++) pos[r] += pos[r - 1];
+            std::vector<int64_t> cur(pos.begin(), pos.end() - 1);
+            for (int64_t i = 0; i < c; i++) {
+                const int64_t r = (int64_t)(k[i] >> 32) - row_lo;
+                cols[cur[r]++] = (int32_t)(uint32_t)k[i];
+            }
+            int64_t d = 0;
+            for (int64_t r = 0; r < nr; r++) {
+                int32_t* a = cols.data() + pos[r];
+                int32_t* e = cols.data() + pos[r + 1];
+                rstart[row_lo + r] = pos[r];
+                std::sort(a, e);
+                deg[row_lo + r] = (int32_t)(std::unique(a, e) - a);
+                d += deg[row_lo + r];
+            }
+            kept[b] = d;
+        }
+    };
+    parallel_for(nt, nt, sort_rows);
+    std::vector<int64_t> kstart(nb + 1, 0);
+    for (int64_t b = 0; b < nb; b++) kstart[b + 1] = kstart[b] + kept[b];
+    const int64_t total = kstart[nb];
+    if (total > INT32_MAX) return total;
+    adj.resize((size_t)std::max<int64_t>(total, 1));
+    off.resize((size_t)n + 1);
+    // concatenate the deduplicated rows
+    next = 0;
+    auto fill = [&](int, int64_t, int64_t) {
+        for (;;) {
+            const int64_t b = next.fetch_add(1);
+            if (b >= nb) break;
+            int64_t row_lo, row_hi;
+            rows_of(b, row_lo, row_hi);
+            int64_t w = kstart[b];
+            for (int64_t r = row_lo; r < row_hi; r++) {
+                off[r] = (int32_t)w;
+                std::copy(cols.data() + rstart[r], cols.data() + rstart[r] + deg[r], adj.data() + w);
+                w += deg[r];
+            }
+        }
+    };
+    parallel_for(nt, nt, fill);
+    off[n] = (int32_t)total;
+    return total;
 }
 
 }  // namespace
@@ -34,58 +153,29 @@ int build_host_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
     if (m < 0) { err = "m must be >= 0"; return XM_EINVAL; }
     if (m > 0 && (!src || !dst)) { err = "NULL arc array"; return XM_EINVAL; }
     std::atomic<bool> bad{false};
-    parallel_for(m, [&](int64_t lo, int64_t hi) {
+    parallel_for(m, n_threads(m), [&](int, int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi; i++)
             if ((uint32_t)src[i] >= (uint32_t)n || (uint32_t)dst[i] >= (uint32_t)n) { bad = true; return; }
     });
     if (bad) { err = "arc endpoint outside [0, n)"; return XM_EINVAL; }
+    // the arc count after deduplication must fit the int32 offsets
+    if (m > (int64_t)INT32_MAX * 2) { err = "too many arcs"; return XM_EINVAL; }
 
-    // bucket by source (self-loops dropped)
-    std::vector<int64_t> off(n + 1, 0);
-    for (int64_t i = 0; i < m; i++)
-        if (src[i] != dst[i]) off[src[i] + 1]++;
-    for (int32_t v = 0; v < n; v++) off[v + 1] += off[v];
-    std::vector<int32_t> adj(std::max<int64_t>(off[n], 1));
-    {
-        std::vector<int64_t> fill(off.begin(), off.end() - 1);
-        for (int64_t i = 0; i < m; i++)
-            if (src[i] != dst[i]) adj[fill[src[i]]++] = dst[i];
-    }
-    // sort each list, drop repeats, record new lengths
-    std::vector<int64_t> len(n + 1, 0);
-    parallel_for(n, [&](int64_t lo, int64_t hi) {
-        for (int64_t v = lo; v < hi; v++) {
-            int32_t* b = adj.data() + off[v];
-            int32_t* e = adj.data() + off[v + 1];
-            std::sort(b, e);
-            len[v] = std::unique(b, e) - b;
-        }
-    });
-    int64_t total = 0;
-    for (int32_t v = 0; v < n; v++) total += len[v];
+    const int64_t total = build_side(
+        n, m, [&](int64_t i) { return ((uint64_t)(uint32_t)src[i] << 32) | (uint32_t)dst[i]; }, G.out_off, G.out_adj);
     if (total > INT32_MAX) { err = "more than 2^31-1 arcs after deduplication"; return XM_EINVAL; }
     G.n = n;
     G.m = total;
-    G.out_off.assign(n + 1, 0);
-    for (int32_t v = 0; v < n; v++) G.out_off[v + 1] = G.out_off[v] + (int32_t)len[v];
-    G.out_adj.resize(std::max<int64_t>(total, 1));
-    parallel_for(n, [&](int64_t lo, int64_t hi) {
+    // in-lists from the deduplicated out-arcs: row of arc i is the source,
+    // found by walking the offsets (build an explicit source array once)
+    HostVec<int32_t> row_of((size_t)std::max<int64_t>(total, 1));
+    parallel_for(n, n_threads(total), [&](int, int64_t lo, int64_t hi) {
         for (int64_t v = lo; v < hi; v++)
-            std::copy(adj.data() + off[v], adj.data() + off[v] + len[v], G.out_adj.data() + G.out_off[v]);
+            for (int32_t i = G.out_off[v]; i < G.out_off[v + 1]; i++) row_of[i] = (int32_t)v;
     });
-    std::vector<int32_t>().swap(adj);
-
-    // in-lists: bucket by destination, scanning sources in ascending order,
-    // so every in-list comes out sorted and free of repeats
-    G.in_off.assign(n + 1, 0);
-    for (int64_t i = 0; i < total; i++) G.in_off[G.out_adj[i] + 1]++;
-    for (int32_t v = 0; v < n; v++) G.in_off[v + 1] += G.in_off[v];
-    G.in_adj.resize(std::max<int64_t>(total, 1));
-    {
-        std::vector<int32_t> fill(G.in_off.begin(), G.in_off.end() - 1);
-        for (int32_t u = 0; u < n; u++)
-            for (int32_t i = G.out_off[u]; i < G.out_off[u + 1]; i++) G.in_adj[fill[G.out_adj[i]]++] = u;
-    }
+    build_side(n, total,
+               [&](int64_t i) { return ((uint64_t)(uint32_t)G.out_adj[i] << 32) | (uint32_t)row_of[i]; }, G.in_off,
+               G.in_adj);
     return XM_OK;
 }
 
