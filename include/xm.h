@@ -58,9 +58,10 @@ enum {
     XM_NO_REDUCE = 1,  /* plan over the original pattern, no reuse of candidate sets
                           (the "XMiner without reduction" variant of Sec. 6.3) */
     XM_EMBEDDINGS = 2, /* count every embedding; no symmetry-breaking conditions */
-    XM_INDUCED = 4     /* induced matching: a pair of pattern vertices without an arc must map to a
+    XM_INDUCED = 4,    /* induced matching: a pair of pattern vertices without an arc must map to a
                           pair of nodes without that arc (DIFF operands); the paper defines only
                           edge and degree constraints, so this is an extension */
+    XM_NO_PRODUCT = 8  /* count by walking every level: no leaf products (see xm_plan_product) */
 };
 
 typedef struct xm_graph_s *xm_graph;
@@ -138,7 +139,8 @@ void xm_graph_free(xm_graph g);
  *   k          pattern vertices, 2 <= k <= 8 (vertices are 0..k-1).
  *   e          pattern arcs, 1 <= e <= k(k-1).
  *   psrc, pdst arc endpoints (host memory), e int32 each.
- *   flags      XM_REDUCE (0) | XM_NO_REDUCE | XM_EMBEDDINGS | XM_INDUCED.
+ *   flags      XM_REDUCE (0) | XM_NO_REDUCE | XM_EMBEDDINGS | XM_INDUCED |
+ *              XM_NO_PRODUCT.
  *   out        receives the plan handle.
  * Errors: XM_EINVAL for a self-loop, a repeated arc, an id outside [0, k),
  * k or e out of range, or a pattern that is not weakly connected.
@@ -199,6 +201,44 @@ typedef struct {
 } xm_level_info;
 
 int xm_plan_level(xm_plan p, int32_t level, xm_level_info *out);
+
+/*
+ * xm_plan_product -- the plan's leaf product (Sec. 5.3: when only the count
+ * is wanted, the sizes of the candidate sets of the vertices left once the
+ * active nodes are matched are multiplied instead of enumerated).
+ *
+ * Unless XM_NO_PRODUCT or XM_INDUCED is given, the compiler looks for 2..3
+ * pattern vertices (up to k-2 when they are interchangeable) that share no
+ * arc and whose removal leaves the pattern weakly connected, and moves them
+ * to the end of the materialisation order. Their candidate sets then depend
+ * only on the nodes matched before them, so xm_count stops at the first of
+ * them (level `level`) and adds, for each partial match, the number of
+ * ways to pick pairwise distinct nodes from the r sets:
+ *   kind 1 (choose): one common set C and a total order imposed by the
+ *     symmetry conditions: C(|C|, r);
+ *   kind 2 (inclusion-exclusion, r <= 3): |C_0||C_1| - |C_0 & C_1| for
+ *     r = 2, and the alternating sum over set partitions for r = 3. The
+ *     paper multiplies the set sizes without correcting for nodes that lie
+ *     in several sets; the correction keeps matches injective.
+ * xm_enumerate ignores the product and walks all k levels.
+ *
+ *   level, r, kind  product level p, number of product vertices r (0: no
+ *                   product), kind (0 none, 1 choose, 2 inclusion-exclusion);
+ *   n_sets          records readable with xm_plan_product_set: 1 for kind 1,
+ *                   2^r - 1 for kind 2.
+ * Any pointer may be NULL. Errors: XM_EINVAL for a NULL plan.
+ */
+int xm_plan_product(xm_plan p, int32_t *level, int32_t *r, int32_t *kind, int32_t *n_sets);
+
+/*
+ * xm_plan_product_set -- set record i of the leaf product, in the layout of
+ * xm_plan_level (vertex = -1; operands, bounds and injectivity refer to
+ * levels < p only; no degree thresholds). Kind 1: record 0 is the common
+ * set. Kind 2: record s - 1 is the intersection of the sets of the product
+ * vertices in bit mask s (bit j = level p + j).
+ * Errors: XM_EINVAL for a NULL plan or i outside [0, n_sets).
+ */
+int xm_plan_product_set(xm_plan p, int32_t i, xm_level_info *out);
 
 /* Frees a plan. NULL is a no-op. */
 void xm_plan_free(xm_plan p);

@@ -19,7 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libxm.so")
 
 XM_OK, XM_EINVAL, XM_ENOMEM, XM_EOVERFLOW, XM_ECUDA, XM_ETIMEOUT, XM_EBUSY = range(7)
-XM_REDUCE, XM_NO_REDUCE, XM_EMBEDDINGS, XM_INDUCED = 0, 1, 2, 4
+XM_REDUCE, XM_NO_REDUCE, XM_EMBEDDINGS, XM_INDUCED, XM_NO_PRODUCT = 0, 1, 2, 4, 8
+XM_PROD_NONE, XM_PROD_CHOOSE, XM_PROD_IE = 0, 1, 2
 
 # every symbol include/xm.h declares
 EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_graph_info", "xm_graph_csr",
@@ -29,7 +30,8 @@ EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_gr
            "xm_count_noalloc", "xm_batch_create", "xm_batch_set_tuning", "xm_batch_get_tuning", "xm_batch_run",
            "xm_batch_run_graph", "xm_batch_counts", "xm_batch_tune", "xm_batch_free", "xm_count_batch",
            "xm_query_bytes", "xm_server_create", "xm_server_submit", "xm_server_poll", "xm_server_info",
-           "xm_server_free", "xm_count_roots", "xm_enumerate_roots", "xm_count_roots_stats", "xm_plan_tune"]
+           "xm_server_free", "xm_count_roots", "xm_enumerate_roots", "xm_count_roots_stats", "xm_plan_tune",
+           "xm_plan_product", "xm_plan_product_set"]
 
 
 class XmError(RuntimeError):
@@ -74,6 +76,8 @@ def _load():
         "xm_plan_info": (ctypes.c_int, [vp, i32p, i32p, i32p, i32p, i32p]),
         "xm_plan_order": (ctypes.c_int, [vp, i32p]),
         "xm_plan_level": (ctypes.c_int, [vp, i32, ctypes.POINTER(xm_level_info)]),
+        "xm_plan_product": (ctypes.c_int, [vp, i32p, i32p, i32p, i32p]),
+        "xm_plan_product_set": (ctypes.c_int, [vp, i32, ctypes.POINTER(xm_level_info)]),
         "xm_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, i32]),
         "xm_plan_free": (None, [vp]),
         "xm_plan_set_tuning": (ctypes.c_int, [vp, ctypes.POINTER(xm_tuning)]),
@@ -210,14 +214,30 @@ class Plan:
         _check(lib().xm_plan_order(self._h, o))
         return list(o)
 
-    def level(self, l: int) -> dict:
-        info = xm_level_info()
-        _check(lib().xm_plan_level(self._h, l, ctypes.byref(info)))
+    @staticmethod
+    def _level_dict(info) -> dict:
         return {"vertex": info.vertex, "ops": [(info.op_level[i], info.op_dir[i]) for i in range(info.nops)],
                 "reuse": info.reuse, "reuse_ops": info.reuse_ops, "dout_min": info.dout_min,
                 "din_min": info.din_min, "lo_mask": info.lo_mask, "hi_mask": info.hi_mask,
                 "neq_mask": info.neq_mask,
                 "diffs": [(info.diff_level[i], info.diff_dir[i]) for i in range(info.ndiff)]}
+
+    def level(self, l: int) -> dict:
+        info = xm_level_info()
+        _check(lib().xm_plan_level(self._h, l, ctypes.byref(info)))
+        return self._level_dict(info)
+
+    def product(self) -> dict:
+        """Leaf product of the plan: level p, r vertices, kind, and its sets."""
+        vals = [ctypes.c_int32() for _ in range(4)]
+        _check(lib().xm_plan_product(self._h, *[ctypes.byref(v) for v in vals]))
+        level, r, kind, n = [v.value for v in vals]
+        sets = []
+        for i in range(n):
+            info = xm_level_info()
+            _check(lib().xm_plan_product_set(self._h, i, ctypes.byref(info)))
+            sets.append(self._level_dict(info))
+        return {"level": level, "r": r, "kind": kind, "sets": sets}
 
     def describe(self) -> str:
         need = lib().xm_plan_describe(self._h, None, 0)

@@ -94,7 +94,7 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
     a.l1root = g->d_l1root;
     a.e_units = g->d_e_units;
     a.emax = (int32_t)std::max<int64_t>(g->m, 1);
-    a.l2_units = use_l2_units(P.dev) ? 1 : 0;
+    a.l2_units = use_l2_units(P.dev, mode != MODE_EMIT) ? 1 : 0;
     a.leaf_kind = a.l2_units ? 0 : leaf_closed_form_kind(P.dev);
     a.block_sums = g->d_block_sums;
     a.n_block_sums = g->n_block_sums;
@@ -329,12 +329,9 @@ int xm_plan_order(xm_plan p, int32_t* order) {
     return XM_OK;
 }
 
-int xm_plan_level(xm_plan p, int32_t level, xm_level_info* out) {
-    if (!p || !out) { set_error("NULL argument"); return XM_EINVAL; }
-    if (level < 0 || level >= p->plan.k) { set_error("level out of range"); return XM_EINVAL; }
-    const XmLevel& L = p->plan.dev.lv[level];
+static void level_record(const XmLevel& L, int32_t vertex, xm_level_info* out) {
     memset(out, 0, sizeof *out);
-    out->vertex = p->plan.dev.order[level];
+    out->vertex = vertex;
     out->nops = L.nops;
     for (int i = 0; i < L.nops; i++) {
         out->op_level[i] = L.op_level[i];
@@ -352,6 +349,29 @@ int xm_plan_level(xm_plan p, int32_t level, xm_level_info* out) {
         out->diff_level[i] = L.diff_level[i];
         out->diff_dir[i] = L.diff_dir[i];
     }
+}
+
+int xm_plan_level(xm_plan p, int32_t level, xm_level_info* out) {
+    if (!p || !out) { set_error("NULL argument"); return XM_EINVAL; }
+    if (level < 0 || level >= p->plan.k) { set_error("level out of range"); return XM_EINVAL; }
+    level_record(p->plan.dev.lv[level], p->plan.dev.order[level], out);
+    return XM_OK;
+}
+
+int xm_plan_product(xm_plan p, int32_t* level, int32_t* r, int32_t* kind, int32_t* n_sets) {
+    if (!p) { set_error("NULL plan"); return XM_EINVAL; }
+    const XmPlanDev& D = p->plan.dev;
+    if (level) *level = D.prod_p;
+    if (r) *r = D.prod_r;
+    if (kind) *kind = D.prod_kind;
+    if (n_sets) *n_sets = D.prod_nv;
+    return XM_OK;
+}
+
+int xm_plan_product_set(xm_plan p, int32_t i, xm_level_info* out) {
+    if (!p || !out) { set_error("NULL argument"); return XM_EINVAL; }
+    if (i < 0 || i >= p->plan.dev.prod_nv) { set_error("product set index out of range"); return XM_EINVAL; }
+    level_record(p->plan.dev.pv[i], -1, out);
     return XM_OK;
 }
 

@@ -261,6 +261,114 @@ void symmetry_conditions(int k, const std::vector<int>& order, std::vector<std::
     }
 }
 
+// ----------------------------------------------------- leaf products (5.3)
+// Sec. 5.3 counts by multiplying the sizes of the candidate sets of the
+// vertices that are still open once the active nodes are matched. Here such
+// vertices form a set I of pattern vertices with no arc between them and a
+// weakly connected rest: with I at the end of the order, every vertex of I
+// is constrained by earlier levels only. A count is then exact when
+//   - no symmetry condition relates two vertices of I (inclusion-exclusion
+//     over the sets removes tuples that repeat a node), r = |I| <= 3; or
+//   - the conditions order I totally and all of I have the same operands
+//     and bounds against the rest (one set C): C(|C|, r) increasing tuples.
+
+struct ProductChoice {
+    int r = 0;
+    int kind = XM_PROD_NONE;
+    std::vector<int> order;
+};
+
+// Order of the vertices outside `drop` (which never holds base[0]): each
+// vertex after the first is the earliest vertex of `base` adjacent to one
+// already placed. Empty when the rest is not weakly connected.
+std::vector<int> prefix_order(const Pat& P, const std::vector<int>& base, uint32_t drop) {
+    std::vector<int> out;
+    uint32_t placed = 0;
+    const int want = P.k - __builtin_popcount(drop);
+    while ((int)out.size() < want) {
+        int pick = -1;
+        for (int v : base) {
+            if ((drop >> v & 1u) || (placed >> v & 1u)) continue;
+            if (placed && !((P.outb[v] | P.inb[v]) & placed)) continue;
+            pick = v;
+            break;
+        }
+        if (pick < 0) return {};
+        out.push_back(pick);
+        placed |= 1u << pick;
+    }
+    return out;
+}
+
+ProductChoice choose_product(const Pat& P, const std::vector<int>& base, const std::vector<std::vector<int>>& aut,
+                             bool symmetry) {
+    const int k = P.k;
+    std::vector<int> pos(k);
+    for (int i = 0; i < k; i++) pos[base[i]] = i;
+    ProductChoice best;
+    long best_score = -1;
+    for (uint32_t I = 1; I < (1u << k); I++) {
+        const int r = __builtin_popcount(I);
+        if (r < 2 || r > k - 2) continue;
+        if (I >> base[0] & 1u) continue;  // the start vertex stays Alg. 1's maxDegree choice
+        bool independent = true;
+        for (int v = 0; v < k && independent; v++)
+            if ((I >> v & 1u) && ((P.outb[v] | P.inb[v]) & I)) independent = false;
+        if (!independent) continue;
+        std::vector<int> order = prefix_order(P, base, I);
+        if (order.empty()) continue;
+        std::vector<int> mem;
+        for (int v : base)
+            if (I >> v & 1u) mem.push_back(v);
+        order.insert(order.end(), mem.begin(), mem.end());
+        uint32_t less[XM_MAXK] = {0};
+        if (symmetry) symmetry_conditions(k, order, aut, less);
+        // direct conditions among I, and their transitive closure
+        uint32_t rel[XM_MAXK] = {0};
+        int direct = 0;
+        for (int a : mem)
+            for (int b : mem)
+                if (less[a] >> b & 1u) { rel[a] |= 1u << b; direct++; }
+        for (int it = 0; it < r; it++)
+            for (int a : mem)
+                for (int b : mem)
+                    if (rel[a] >> b & 1u) rel[a] |= rel[b];
+        int kind = XM_PROD_NONE;
+        if (direct == 0) {
+            if (r <= 3) kind = XM_PROD_IE;
+        } else {
+            bool total = true;
+            for (int a : mem)
+                for (int b : mem)
+                    if (a != b && !((rel[a] >> b & 1u) || (rel[b] >> a & 1u))) total = false;
+            bool same = true;
+            const uint32_t rest = ((1u << k) - 1) & ~I;
+            for (int b : mem)
+                for (int w = 0; w < k; w++) {
+                    if (!(rest >> w & 1u)) continue;
+                    const int a = mem[0];
+                    if (P.arc(w, a) != P.arc(w, b) || P.arc(a, w) != P.arc(b, w) ||
+                        ((less[w] >> a) & 1u) != ((less[w] >> b) & 1u) || ((less[a] >> w) & 1u) != ((less[b] >> w) & 1u))
+                        same = false;
+                }
+            if (total && same) kind = XM_PROD_CHOOSE;
+        }
+        if (kind == XM_PROD_NONE) continue;
+        // more product vertices first, then one common set, then the set
+        // whose vertices come latest in the reduction's order
+        long late = 0;
+        for (int v : mem) late += pos[v];
+        const long score = (long)r * 10000 + (kind == XM_PROD_CHOOSE ? 1000 : 0) + late;
+        if (score > best_score) {
+            best_score = score;
+            best.r = r;
+            best.kind = kind;
+            best.order = order;
+        }
+    }
+    return best;
+}
+
 }  // namespace
 
 // --------------------------------------------------------------- compile ---
@@ -270,7 +378,7 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
     if (k < 2 || k > XM_MAXK) { err = "k must be in [2, 8]"; return XM_EINVAL; }
     if (e < 1 || e > k * (k - 1)) { err = "arc count out of range"; return XM_EINVAL; }
     if (!psrc || !pdst) { err = "NULL arc array"; return XM_EINVAL; }
-    if (flags & ~(XM_NO_REDUCE | XM_EMBEDDINGS | XM_INDUCED)) { err = "unknown flag"; return XM_EINVAL; }
+    if (flags & ~(XM_NO_REDUCE | XM_EMBEDDINGS | XM_INDUCED | XM_NO_PRODUCT)) { err = "unknown flag"; return XM_EINVAL; }
     Pat P;
     P.k = k;
     P.e = e;
@@ -308,6 +416,11 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
     red.run();
     const Reduction& R = red.R;
     std::vector<int> order = materialisation_order(P, R);
+    ProductChoice pc;
+    if (!(flags & (XM_INDUCED | XM_NO_PRODUCT)) && k >= 4) {
+        pc = choose_product(P, order, aut, !(flags & XM_EMBEDDINGS));
+        if (pc.r) order = pc.order;
+    }
 
     uint32_t less[XM_MAXK];
     if (flags & XM_EMBEDDINGS)
@@ -446,6 +559,90 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
         if (L.dout_min <= nin) L.dout_min = 0;
     }
 
+    // Leaf-product sets: each is a level over the prefix p = k - r, with the
+    // operands, order bounds (against the prefix) of its member levels and
+    // injectivity against the prefix nodes no operand or bound excludes.
+    // It may start from a complete prefix set (Sec. 5.2) whose operands it
+    // contains, whose bounds hold for it and whose degree thresholds every
+    // member's candidates meet.
+    if (pc.r) {
+        const int p = k - pc.r;
+        const uint32_t prefix = (1u << p) - 1;
+        D.prod_p = p;
+        D.prod_r = pc.r;
+        D.prod_kind = pc.kind;
+        D.prod_nv = pc.kind == XM_PROD_CHOOSE ? 1 : (1 << pc.r) - 1;
+        for (int si = 0; si < D.prod_nv; si++) {
+            const uint32_t members = (uint32_t)si + 1;
+            XmLevel& V = D.pv[si];
+            memset(&V, 0, sizeof V);
+            V.reuse = -1;
+            uint32_t adj = 0, mverts = 0;
+            int dmax_out = 0, dmax_in = 0;
+            for (int j = 0; j < pc.r; j++) {
+                if (!(members >> j & 1u)) continue;
+                const XmLevel& M = D.lv[p + j];
+                const int v = order[p + j];
+                mverts |= 1u << v;
+                for (int i = 0; i < M.nops; i++) {
+                    bool have = false;
+                    for (int q = 0; q < V.nops; q++)
+                        if (V.op_level[q] == M.op_level[i] && V.op_dir[q] == M.op_dir[i]) have = true;
+                    if (!have) {
+                        V.op_level[V.nops] = M.op_level[i];
+                        V.op_dir[V.nops] = M.op_dir[i];
+                        V.nops++;
+                    }
+                    adj |= 1u << M.op_level[i];
+                }
+                V.lo_mask |= M.lo_mask & prefix;
+                V.hi_mask |= M.hi_mask & prefix;
+                dmax_out = std::max(dmax_out, P.dout[v]);
+                dmax_in = std::max(dmax_in, P.din[v]);
+            }
+            V.neq_mask = prefix & ~adj & ~V.lo_mask & ~V.hi_mask;
+            if (!reduce) continue;
+            int best = -1, best_ops = 0;
+            uint32_t best_mask = 0;
+            for (int r = 1; r < p; r++) {
+                const XmLevel& Rl = D.lv[r];
+                if (Rl.nops == 0 || Rl.ndiff) continue;
+                if (Rl.dout_min > dmax_out || Rl.din_min > dmax_in) continue;
+                uint32_t mask = 0;
+                bool subset = true;
+                for (int i = 0; i < Rl.nops && subset; i++) {
+                    int found = -1;
+                    for (int q = 0; q < V.nops; q++)
+                        if (V.op_level[q] == Rl.op_level[i] && V.op_dir[q] == Rl.op_dir[i]) found = q;
+                    if (found < 0) subset = false; else mask |= 1u << found;
+                }
+                if (!subset) continue;
+                bool bounds_ok = true;
+                for (int j = 0; j < r && bounds_ok; j++) {
+                    const int u = order[j];
+                    bool lo_implied = false, hi_implied = false;
+                    for (int v = 0; v < k; v++) {
+                        if (!(mverts >> v & 1u)) continue;
+                        if (lt[u] >> v & 1u) lo_implied = true;
+                        if (lt[v] >> u & 1u) hi_implied = true;
+                    }
+                    if ((Rl.lo_mask >> j & 1u) && !lo_implied) bounds_ok = false;
+                    if ((Rl.hi_mask >> j & 1u) && !hi_implied) bounds_ok = false;
+                }
+                if (!bounds_ok) continue;
+                if (Rl.nops > best_ops || (Rl.nops == best_ops && r > best)) {
+                    best = r;
+                    best_ops = Rl.nops;
+                    best_mask = mask;
+                }
+            }
+            if (best >= 0) {
+                V.reuse = best;
+                V.reuse_ops = best_mask;
+            }
+        }
+    }
+
     out.dev = D;
     out.k = k;
     out.e = e;
@@ -496,6 +693,23 @@ std::string describe_plan(const Plan& p) {
             s += buf;
         }
         s += "\n";
+    }
+    if (D.prod_r) {
+        snprintf(buf, sizeof buf, "product: level %d r=%d kind=%s sets=%d\n", D.prod_p, D.prod_r,
+                 D.prod_kind == XM_PROD_CHOOSE ? "choose" : "incl-excl", D.prod_nv);
+        s += buf;
+        for (int i = 0; i < D.prod_nv; i++) {
+            const XmLevel& V = D.pv[i];
+            snprintf(buf, sizeof buf, "P%d ops:", i + 1);
+            s += buf;
+            for (int q = 0; q < V.nops; q++) {
+                snprintf(buf, sizeof buf, " %s(L%d)", V.op_dir[q] == XM_DIR_OUT ? "out" : "in", V.op_level[q]);
+                s += buf;
+            }
+            snprintf(buf, sizeof buf, " reuse=%d/0x%x lo=0x%x hi=0x%x neq=0x%x\n", V.reuse, V.reuse_ops, V.lo_mask,
+                     V.hi_mask, V.neq_mask);
+            s += buf;
+        }
     }
     return s;
 }

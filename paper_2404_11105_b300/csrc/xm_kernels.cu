@@ -273,7 +273,8 @@ __device__ __forceinline__ int32_t root_node(const RunArgs& ra, int i) {
 // Chunks of the first-level driver list per start node (0 when the node
 // fails the start vertex's degree filter or lies outside [r_lo, r_hi)).
 __global__ void k_l1_chunks(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
-    __shared__ XmPlanDev P;
+    __shared__ __align__(16) unsigned char pbuf[plan_bytes(XM_MAXK)];
+    XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(pbuf);
     plan_to_smem(P, plan_g);
     const GraphDev& g = ra.g;
     const int ni = ra.n_idx;
@@ -294,7 +295,8 @@ __global__ void k_l1_chunks(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
 // chunk_cnt[c]; WRITE=true writes them at the scanned offset chunk_cnt[c].
 template <bool WRITE, int MODE>
 __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
-    __shared__ XmPlanDev P;
+    __shared__ __align__(16) unsigned char pbuf[plan_bytes(XM_MAXK)];
+    XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(pbuf);
     plan_to_smem(P, plan_g);
     const GraphDev& g = ra.g;
     const int ni = ra.n_idx;
@@ -406,8 +408,7 @@ __global__ void k_units(RunArgs ra) {
 // (or a complete earlier set in their place), driver, probes and the cut of
 // the driver by the order bounds. Returns algorithmic bytes (stats).
 template <int MODE>
-__device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane) {
-    const XmLevel& L = P.lv[l];
+__device__ unsigned long long setup_lists(const XmLevel& L, const GraphDev& g, WarpSmem& ws, LvState& S, int lane) {
     int32_t lo, hi;
     level_bounds(L, ws.m, lo, hi);
     ListRef lists[XM_MAXOPS + 1];
@@ -450,7 +451,6 @@ __device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g,
     if (c0 >= c1) empty = true;
     unsigned long long bytes = 0;
     if (lane == 0) {
-        LvState& S = ws.st[l];
         S.drv = lists[d].p;
         S.drv_shared = lists[d].shared;
         int np = 0, psh = 0;
@@ -489,15 +489,20 @@ __device__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g,
     return bytes;
 }
 
+template <int MODE>
+__device__ __forceinline__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l,
+                                                          int lane) {
+    return setup_lists<MODE>(P.lv[l], g, ws, ws.st[l], lane);
+}
+
 // Runs the driver range [drv_pos, drv_end) of level l through probes and
 // filters 32 ids at a time. With WINDOW the survivors are compacted into
 // `win` (stopping when fewer than 32 slots are left); otherwise they are
 // counted or emitted.
 template <int MODE, bool WINDOW>
-__device__ unsigned long long scan_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, LvState& S, int l,
-                                         int32_t* win, int W, int lane, const RunArgs& ra,
+__device__ unsigned long long scan_level(const XmPlanDev& P, const XmLevel& L, const GraphDev& g, WarpSmem& ws,
+                                         LvState& S, int l, int32_t* win, int W, int lane, const RunArgs& ra,
                                          unsigned long long& stat_bytes) {
-    const XmLevel& L = P.lv[l];
     const bool dsh = S.drv_shared;
     const int np = S.nprobe;
     int32_t plo[XM_MAXOPS];
@@ -604,6 +609,32 @@ __device__ unsigned long long leaf_count_hashed(const XmLevel& L, WarpSmem& ws, 
     return lane == 0 ? cnt : 0;
 }
 
+// Count (or emit) the candidates of level l's set S, already set up from
+// record L, over the driver range [pos, end). The count is on lane 0.
+template <int MODE>
+__device__ unsigned long long leaf_tail(const XmPlanDev& P, const XmLevel& L, const GraphDev& g, WarpSmem& ws,
+                                        LvState& S, int l, int lane, const RunArgs& ra, unsigned long long& stat_bytes,
+                                        unsigned long long& leaf_elems, int pos, int end) {
+    if (MODE == MODE_STATS && lane == 0) leaf_elems += end - pos;
+    if (MODE != MODE_EMIT && S.nprobe == 0 && L.ndiff == 0) {
+        // A single list: its size, minus already matched nodes inside it.
+        unsigned long long c = end - pos;
+        for (uint32_t nm = L.neq_mask; nm; nm &= nm - 1) {
+            const int32_t y = ws.m[__ffs(nm) - 1];
+            const int q = lbound(S.drv, pos, end, y, S.drv_shared);
+            if (q < end && ld(S.drv, q, S.drv_shared) == y) c--;
+        }
+        return lane == 0 ? c : 0;
+    }
+    if (MODE == MODE_COUNT && L.ndiff == 0) {
+        bool hashed = S.probe_shared == 0;
+        for (int p = 0; p < S.nprobe && hashed; p++) hashed = S.pT[p] != 0;
+        if (hashed) return leaf_count_hashed(L, ws, S, lane);
+    }
+    unsigned long long r = scan_level<MODE, false>(P, L, g, ws, S, l, nullptr, 0, lane, ra, stat_bytes);
+    return lane == 0 ? r : 0;
+}
+
 // Count (or emit) the candidates of the last level l >= 2.
 template <int MODE>
 __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane,
@@ -621,25 +652,66 @@ __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, 
         S.drv_end = end;
     }
     __syncwarp();
-    if (MODE == MODE_STATS && lane == 0) leaf_elems += end - pos;
-    const XmLevel& L = P.lv[l];
-    if (MODE != MODE_EMIT && S.nprobe == 0 && L.ndiff == 0) {
-        // A single list: its size, minus already matched nodes inside it.
-        unsigned long long c = end - pos;
-        for (uint32_t nm = L.neq_mask; nm; nm &= nm - 1) {
-            const int32_t y = ws.m[__ffs(nm) - 1];
-            const int q = lbound(S.drv, pos, end, y, S.drv_shared);
-            if (q < end && ld(S.drv, q, S.drv_shared) == y) c--;
-        }
-        return lane == 0 ? c : 0;
+    return leaf_tail<MODE>(P, P.lv[l], g, ws, S, l, lane, ra, stat_bytes, leaf_elems, pos, end);
+}
+
+// Adds a 128-bit value on lane 0 to the lane's running count, or straight to
+// the 128-bit counter when the 64-bit count would wrap.
+__device__ __forceinline__ void add_count(unsigned long long& acc, unsigned __int128 v, unsigned long long* counter,
+                                          int lane) {
+    if (lane != 0 || v == 0) return;
+    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    if (hi == 0 && acc + lo >= acc) {
+        acc += lo;
+        return;
     }
-    if (MODE == MODE_COUNT && L.ndiff == 0) {
-        bool hashed = S.probe_shared == 0;
-        for (int p = 0; p < S.nprobe && hashed; p++) hashed = S.pT[p] != 0;
-        if (hashed) return leaf_count_hashed(L, ws, S, lane);
+    const unsigned long long old = atomicAdd(counter, lo);
+    const unsigned long long carry = (old + lo < old) ? 1 : 0;
+    if (hi + carry) atomicAdd(counter + 1, hi + carry);
+}
+
+// Leaf product at level l = prod_p (Sec. 5.3): the sizes of the product
+// sets pv[] under the partial match m_0..m_{l-1}, combined into the number
+// of tuples of pairwise distinct nodes (see XmPlanDev).
+template <int MODE>
+__device__ __noinline__ unsigned __int128 leaf_product(const XmPlanDev& P, const XmLevel* __restrict__ pv, const GraphDev& g,
+                                          WarpSmem& ws, int l, int lane, const RunArgs& ra,
+                                          unsigned long long& stat_bytes, unsigned long long& leaf_elems) {
+    LvState& S = ws.st[l];
+    auto size_of = [&](int i) -> unsigned long long {
+        const XmLevel& V = pv[i];
+        stat_bytes += setup_lists<MODE>(V, g, ws, S, lane);
+        unsigned long long c = 0;
+        if (!S.empty) c = leaf_tail<MODE>(P, V, g, ws, S, l, lane, ra, stat_bytes, leaf_elems, S.c0, S.c1);
+        return __shfl_sync(FULL, c, 0);
+    };
+    typedef unsigned __int128 u128;
+    const int r = P.prod_r;
+    if (P.prod_kind == XM_PROD_CHOOSE) {
+        const unsigned long long c = size_of(0);
+        if (c < (unsigned long long)r) return 0;
+        // C(c, r) = prod_{i<r} (c - i) / (i + 1), exact after every step
+        u128 t = 1;
+        for (int i = 0; i < r; i++) t = t * (u128)(c - i) / (u128)(i + 1);
+        return t;
     }
-    unsigned long long r = scan_level<MODE, false>(P, g, ws, S, l, nullptr, 0, lane, ra, stat_bytes);
-    return lane == 0 ? r : 0;
+    if (r == 2) {
+        const unsigned long long a = size_of(0);
+        if (!a) return 0;
+        const unsigned long long b = size_of(1);
+        if (!b) return 0;
+        const unsigned long long ab = size_of(2);
+        return (u128)a * b - ab;
+    }
+    // r == 3; set s - 1 holds the intersection over the members in mask s
+    const unsigned long long s1 = size_of(0);
+    if (!s1) return 0;
+    const unsigned long long s2 = size_of(1);
+    if (!s2) return 0;
+    const unsigned long long s4 = size_of(3);
+    if (!s4) return 0;
+    const unsigned long long s3 = size_of(2), s5 = size_of(4), s6 = size_of(5), s7 = size_of(6);
+    return (u128)s1 * s2 * s4 - (u128)s3 * s4 - (u128)s5 * s2 - (u128)s6 * s1 + (u128)2 * s7;
 }
 
 struct Stats {
@@ -654,7 +726,7 @@ __device__ bool descend(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
     if (MODE == MODE_STATS && lane == 0) st.sets++;
     LvState& N = ws.st[nl];
     if (N.empty) return false;
-    scan_level<MODE, true>(P, g, ws, N, nl, win, W, lane, ra, st.bytes);
+    scan_level<MODE, true>(P, P.lv[nl], g, ws, N, nl, win, W, lane, ra, st.bytes);
     if (lane == 0) {
         N.complete = N.drv_pos >= N.drv_end;
         N.it_ptr = win;
@@ -671,11 +743,13 @@ __device__ bool descend(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
 
 // Depth-first extension below the first level (Alg. 2 Explore): level 1's
 // iteration state is set; levels wl0.. use windows wins + (l - wl0) * W;
-// the last level is counted (or emitted) into acc.
-template <int MODE>
+// the last level is counted (or emitted) into acc. With PROD (counting with
+// a leaf product, sets ra.pv) the walk ends at level prod_p, which adds the
+// product (values past 64 bits go straight to the global counter).
+template <int MODE, bool PROD>
 __device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* wins, int W, int wl0, int lane,
                         const RunArgs& ra, unsigned long long& acc, Stats& st, const Budget& budget, int l0 = 1) {
-    const int k = P.k;
+    const int k = PROD ? P.prod_p + 1 : P.k;
     int l = l0;
     unsigned steps = 0;
     while (l >= l0) {
@@ -685,7 +759,7 @@ __device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
             if (S.complete || S.drv_pos >= S.drv_end) { l--; continue; }
             if (lane == 0) { S.wcnt = 0; S.wpos = 0; }
             __syncwarp();
-            scan_level<MODE, true>(P, g, ws, S, l, wins + (size_t)(l - wl0) * W, W, lane, ra, st.bytes);
+            scan_level<MODE, true>(P, P.lv[l], g, ws, S, l, wins + (size_t)(l - wl0) * W, W, lane, ra, st.bytes);
             if (lane == 0) S.it_hi = S.wcnt;
             __syncwarp();
             continue;
@@ -696,7 +770,11 @@ __device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
         __syncwarp();
         if (MODE == MODE_STATS && lane == 0) st.ext++;
         if (l + 1 == k - 1) {
-            acc += leaf_level<MODE>(P, g, ws, l + 1, lane, ra, st.bytes, st.leaf);
+            if (PROD)
+                add_count(acc, leaf_product<MODE>(P, ra.pv, g, ws, l + 1, lane, ra, st.bytes, st.leaf),
+                          ra.ctl + CTL_COUNT_LO, lane);
+            else
+                acc += leaf_level<MODE>(P, g, ws, l + 1, lane, ra, st.bytes, st.leaf);
             if (MODE == MODE_STATS && lane == 0) st.sets++;
             continue;
         }
@@ -795,7 +873,8 @@ __device__ void level2_cut(const XmPlanDev& P, const GraphDev& g, int32_t m0, in
 // vertices): its second-level driver range cut into pieces, so the work
 // below one hub is spread over many warps. One thread per candidate.
 __global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
-    __shared__ XmPlanDev P;
+    __shared__ __align__(16) unsigned char pbuf[plan_bytes(XM_MAXK)];
+    XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(pbuf);
     plan_to_smem(P, plan_g);
     const int E = set_start(ra, ra.n_idx);
     const int per = P.k == 3 ? LEAF_UNIT : ra.unit;
@@ -861,7 +940,7 @@ __device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDe
     return acc;
 }
 
-template <int MODE>
+template <int MODE, bool PROD>
 __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     extern __shared__ __align__(16) unsigned char smem[];
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(smem);
@@ -870,6 +949,9 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int k = P.k;
+    // counting with a leaf product walks levels 0..prod_p only (ke levels)
+    constexpr bool prod = PROD;
+    const int ke = prod ? P.prod_p + 1 : k;
     const int W = ra.window;
     const size_t warp_bytes = warp_state_bytes(k) + (size_t)n_windows(k) * W * sizeof(int32_t);
     unsigned char* wbase = smem + plan_bytes(k) + (size_t)wib * warp_bytes;
@@ -883,7 +965,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
     const int nidx = two_level ? ra.n_idx : ra.emax;
     const int total = uprefix[nidx];
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int per2 = k == 3 ? LEAF_UNIT : ra.unit;
+    const int per2 = ke == 3 ? LEAF_UNIT : ra.unit;
 
     unsigned long long acc = 0;
     Stats st;
@@ -911,7 +993,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
             }
             const int chunk = u - __ldg(uprefix + owner);
             if (MODE == MODE_STATS && lane == 0) st.units++;
-            if (two_level && k > 2) {
+            if (two_level && ke > 2) {
                 // unit = (start node, a piece of its first-level set)
                 const int root = owner;
                 const int s0 = set_start(ra, root), s1 = set_start(ra, root + 1);
@@ -937,7 +1019,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                     S1.drv_pos = S1.drv_end = 0;
                 }
                 __syncwarp();
-                if (!explore<MODE>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget, 1)) stop = true;
+                if (!explore<MODE, PROD>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget, 1)) stop = true;
                 continue;
             }
             if (two_level) {
@@ -983,7 +1065,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
             }
             __syncwarp();
             if (MODE == MODE_STATS && lane == 0) st.ext++;
-            if (k == 3) {
+            if (ke == 3) {
                 acc += leaf_level<MODE>(P, g, ws, 2, lane, ra, st.bytes, st.leaf, chunk * per2, per2);
                 if (MODE == MODE_STATS && lane == 0) st.sets++;
                 continue;
@@ -1002,7 +1084,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
             }
             __syncwarp();
             int32_t* win = wins;  // level 2's window
-            scan_level<MODE, true>(P, g, ws, S2, 2, win, W, lane, ra, st.bytes);
+            scan_level<MODE, true>(P, P.lv[2], g, ws, S2, 2, win, W, lane, ra, st.bytes);
             if (lane == 0) {
                 S2.complete = whole && S2.drv_pos >= S2.drv_end;
                 S2.it_ptr = win;
@@ -1014,7 +1096,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                 S2.set_shared = 1;
             }
             __syncwarp();
-            if (!explore<MODE>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget, 2)) stop = true;
+            if (!explore<MODE, PROD>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget, 2)) stop = true;
         }
         if (stop) break;
     }
@@ -1093,7 +1175,10 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
                     continue;
                 }
                 if (!descend<MODE_COUNT>(P, g, ws, wins, W, 1, lane, ra, st)) continue;
-                if (!explore<MODE_COUNT>(P, g, ws, wins, W, 1, lane, ra, acc, st, budget)) { stop = true; break; }
+                if (!explore<MODE_COUNT, false>(P, g, ws, wins, W, 1, lane, ra, acc, st, budget)) {
+                    stop = true;
+                    break;
+                }
             }
             if (stop) break;
         }
@@ -1245,7 +1330,10 @@ int leaf_closed_form_kind(const XmPlanDev& P) {
     return 0;
 }
 
-bool use_l2_units(const XmPlanDev& P) {
+bool use_l2_units(const XmPlanDev& P, bool counting) {
+    // a leaf product at level 2 takes whole first-level candidates: units
+    // per start node; deeper products split below the first level
+    if (counting && P.prod_r > 0) return P.prod_p >= 3;
     if (P.k < 3) return false;
     if (P.k > 3) return true;
     // three vertices: split below the first level only when the last level
@@ -1262,34 +1350,43 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
     int dev = 0, nsm = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if (a.pv) return cudaErrorInvalidValue;  // set here only
+    RunArgs b = a;
+    // counting passes evaluate the plan's leaf product from the device copy
+    if (mode != MODE_EMIT && P.prod_r > 0)
+        b.pv = reinterpret_cast<const XmLevel*>(reinterpret_cast<const unsigned char*>(plan_dev) +
+                                                offsetof(XmPlanDev, pv));
     if (ev && (err = cudaEventRecord(ev[0], stream)) != cudaSuccess) return err;
     const int grid_nodes = (int)std::min<int64_t>((len + 255) / 256, (int64_t)nsm * 16);
     // 1. first-level candidate sets
-    k_l1_chunks<<<grid_nodes, 256, 0, stream>>>(plan_dev, a);
-    if ((err = scan_in_place(a.root_chunks, len, a, stream)) != cudaSuccess) return err;
+    k_l1_chunks<<<grid_nodes, 256, 0, stream>>>(plan_dev, b);
+    if ((err = scan_in_place(b.root_chunks, len, b, stream)) != cudaSuccess) return err;
     const int grid_chunks = nsm * 8;  // 256-thread blocks: 8 warps each
     if (mode == MODE_STATS)
-        k_l1<false, MODE_STATS><<<grid_chunks, 256, 0, stream>>>(plan_dev, a);
+        k_l1<false, MODE_STATS><<<grid_chunks, 256, 0, stream>>>(plan_dev, b);
     else
-        k_l1<false, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, a);
-    if ((err = scan_in_place(a.chunk_cnt, (int64_t)a.cmax + 1, a, stream)) != cudaSuccess) return err;
-    k_l1<true, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, a);
+        k_l1<false, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, b);
+    if ((err = scan_in_place(b.chunk_cnt, (int64_t)b.cmax + 1, b, stream)) != cudaSuccess) return err;
+    k_l1<true, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, b);
     // 2. work units: per start node for two-vertex patterns, else per
     // first-level candidate (pieces of the second level's driver range)
-    if (!a.l2_units) {
-        k_units<<<grid_nodes, 256, 0, stream>>>(a);
-        if ((err = scan_in_place(a.units, len, a, stream)) != cudaSuccess) return err;
+    if (!b.l2_units) {
+        k_units<<<grid_nodes, 256, 0, stream>>>(b);
+        if ((err = scan_in_place(b.units, len, b, stream)) != cudaSuccess) return err;
     } else {
-        const int grid_e = (int)std::min<int64_t>(((int64_t)a.emax + 256) / 256, (int64_t)nsm * 16);
-        k_l2_units<<<grid_e, 256, 0, stream>>>(plan_dev, a);
-        if ((err = scan_in_place(a.e_units, (int64_t)a.emax + 1, a, stream)) != cudaSuccess) return err;
+        const int grid_e = (int)std::min<int64_t>(((int64_t)b.emax + 256) / 256, (int64_t)nsm * 16);
+        k_l2_units<<<grid_e, 256, 0, stream>>>(plan_dev, b);
+        if ((err = scan_in_place(b.e_units, (int64_t)b.emax + 1, b, stream)) != cudaSuccess) return err;
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // 3. persistent matcher
-    const size_t smem = match_smem_bytes(P.k, a.window, warps_per_block);
-    const void* fn = mode == MODE_STATS ? (const void*)k_match<MODE_STATS>
-                     : mode == MODE_EMIT ? (const void*)k_match<MODE_EMIT>
-                                         : (const void*)k_match<MODE_COUNT>;
+    const size_t smem = match_smem_bytes(P.k, b.window, warps_per_block);
+    const bool prod = b.pv != nullptr;
+    const void* fn = mode == MODE_STATS ? (prod ? (const void*)k_match<MODE_STATS, true>
+                                                : (const void*)k_match<MODE_STATS, false>)
+                     : mode == MODE_EMIT ? (const void*)k_match<MODE_EMIT, false>
+                     : prod              ? (const void*)k_match<MODE_COUNT, true>
+                                         : (const void*)k_match<MODE_COUNT, false>;
     if ((err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return err;
     int occ = 0;
@@ -1299,12 +1396,16 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
     int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, occ) : occ;
     dim3 grid(nsm * bps), block(warps_per_block * 32);
     if (ev && (err = cudaEventRecord(ev[1], stream)) != cudaSuccess) return err;
-    if (mode == MODE_STATS)
-        k_match<MODE_STATS><<<grid, block, smem, stream>>>(plan_dev, a);
+    if (mode == MODE_STATS && prod)
+        k_match<MODE_STATS, true><<<grid, block, smem, stream>>>(plan_dev, b);
+    else if (mode == MODE_STATS)
+        k_match<MODE_STATS, false><<<grid, block, smem, stream>>>(plan_dev, b);
     else if (mode == MODE_EMIT)
-        k_match<MODE_EMIT><<<grid, block, smem, stream>>>(plan_dev, a);
+        k_match<MODE_EMIT, false><<<grid, block, smem, stream>>>(plan_dev, b);
+    else if (prod)
+        k_match<MODE_COUNT, true><<<grid, block, smem, stream>>>(plan_dev, b);
     else
-        k_match<MODE_COUNT><<<grid, block, smem, stream>>>(plan_dev, a);
+        k_match<MODE_COUNT, false><<<grid, block, smem, stream>>>(plan_dev, b);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (ev && (err = cudaEventRecord(ev[2], stream)) != cudaSuccess) return err;
     return cudaSuccess;

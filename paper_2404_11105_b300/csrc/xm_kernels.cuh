@@ -91,6 +91,8 @@ struct RunArgs {
     unsigned long long budget_ns;  // matcher time budget (0: none)
     int32_t* out;               // enumeration buffer (k ints per match)
     unsigned long long capacity;
+    const XmLevel* pv = nullptr;  // leaf-product sets of the device plan when counting
+                                  // with a product (set by launch_match), else null
 };
 
 enum { MODE_COUNT = 0, MODE_STATS = 1, MODE_EMIT = 2 };
@@ -131,8 +133,9 @@ int64_t chunk_capacity(int32_t n, int64_t m);
 // Bytes of shared memory a block of `warps` warps needs.
 size_t match_smem_bytes(int k, int window, int warps);
 
-// Whether a plan's work units split below the first level (RunArgs::l2_units).
-bool use_l2_units(const XmPlanDev& P);
+// Whether a plan's work units split below the first level (RunArgs::l2_units)
+// for a counting (count/stats) or an enumerating pass.
+bool use_l2_units(const XmPlanDev& P, bool counting);
 // 0, or the closed form that counts a three-vertex plan's last level
 // without an intersection per partial match (RunArgs::leaf_kind).
 int leaf_closed_form_kind(const XmPlanDev& P);

@@ -98,7 +98,7 @@ extern "C" int xm_count_noalloc(const int32_t* out_off, const int32_t* out_adj, 
     a.units = reinterpret_cast<int32_t*>(q); q += b_nodes;
     a.e_units = reinterpret_cast<int32_t*>(q); q += b_e;
     a.emax = (int32_t)emax;
-    a.l2_units = use_l2_units(p->plan.dev) ? 1 : 0;
+    a.l2_units = use_l2_units(p->plan.dev, true) ? 1 : 0;
     a.leaf_kind = a.l2_units ? 0 : leaf_closed_form_kind(p->plan.dev);
     a.block_sums = reinterpret_cast<int64_t*>(q); q += b_sums;
     a.ctl = reinterpret_cast<unsigned long long*>(q);

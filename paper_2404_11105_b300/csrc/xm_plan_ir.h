@@ -48,8 +48,31 @@ struct XmLevel {
     int32_t diff_dir[XM_MAXOPS];
 };
 
+// Leaf products (Sec. 5.3: a count multiplies the sizes of the candidate
+// sets of the vertices still open once the active nodes are fixed). When
+// prod_r > 0 the last r = prod_r levels p = prod_p .. k-1 match pattern
+// vertices that share no arc, so each one's candidate set depends on levels
+// < p only; counting stops at level p and adds, per partial match
+// m_0..m_{p-1}, the number of tuples of pairwise distinct nodes drawn one
+// from each set:
+//   XM_PROD_CHOOSE: the r sets are one set C (same operands and bounds) and
+//     the symmetry conditions order the r vertices totally: C(|C|, r);
+//     pv[0] describes C;
+//   XM_PROD_IE (r <= 3): sets C_0..C_{r-1}; inclusion-exclusion over the
+//     set partitions of the r vertices: r = 2: |C_0||C_1| - |C_0 & C_1|;
+//     r = 3: |C_0||C_1||C_2| - |C_0&C_1||C_2| - |C_0&C_2||C_1|
+//            - |C_1&C_2||C_0| + 2|C_0&C_1&C_2|;
+//     pv[s - 1] describes the intersection over the members in bitmask s.
+// A pv[] record is a level over operands of levels < p (order bounds and
+// injectivity against those levels only, no degree filter). Enumeration
+// ignores the products and walks all k levels.
+#define XM_MAXPV 7
+enum { XM_PROD_NONE = 0, XM_PROD_CHOOSE = 1, XM_PROD_IE = 2 };
+
 struct XmPlanDev {
     int32_t k;
     int32_t order[XM_MAXK];  // pattern vertex of each level
+    int32_t prod_p, prod_r, prod_kind, prod_nv;
     XmLevel lv[XM_MAXK];
+    XmLevel pv[XM_MAXPV];
 };

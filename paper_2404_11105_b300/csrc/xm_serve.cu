@@ -163,7 +163,7 @@ int xm_server_submit(xm_server s, xm_plan p, int32_t graph_index, int64_t tag, i
     a.units = reinterpret_cast<int32_t*>(q); q += L.nodes;
     a.e_units = reinterpret_cast<int32_t*>(q); q += L.e;
     a.emax = (int32_t)L.emax;
-    a.l2_units = use_l2_units(p->plan.dev) ? 1 : 0;
+    a.l2_units = use_l2_units(p->plan.dev, true) ? 1 : 0;
     a.leaf_kind = a.l2_units ? 0 : leaf_closed_form_kind(p->plan.dev);
     a.block_sums = reinterpret_cast<int64_t*>(q); q += L.sums;
     a.ctl = reinterpret_cast<unsigned long long*>(q); q += L.ctl;

@@ -172,3 +172,100 @@ def test_induced_plans_vs_oracle(pattern):
         assert run_plan(n, out, inn, p) == g.count_matches(pattern, induced=True)
     pe = xm.Plan(pattern, xm.XM_INDUCED | xm.XM_EMBEDDINGS)
     assert run_plan(n, out, inn, pe) == g.count_embeddings(pattern, induced=True)
+
+
+# ------------------------------------------------ leaf products (Sec. 5.3)
+
+PRODUCT_PATTERNS = {
+    "star4": (4, [(0, 1), (0, 2), (0, 3)]),
+    "instar4": (4, [(1, 0), (2, 0), (3, 0)]),
+    "path4": (4, [(0, 1), (1, 2), (2, 3)]),
+    "mixstar": (4, [(0, 1), (2, 0), (0, 3)]),
+    "star5": (5, [(0, 1), (0, 2), (0, 3), (0, 4)]),
+    "tri_tail": (5, [(0, 1), (1, 2), (0, 2), (2, 3), (2, 4)]),
+    "recip_star": (5, [(0, 1), (1, 0), (0, 2), (2, 0), (0, 3), (0, 4)]),
+    "fan3": (5, [(0, 1), (0, 2), (0, 3), (4, 1), (4, 2), (4, 3)]),
+    "path5": (5, [(0, 1), (1, 2), (2, 3), (3, 4)]),
+    "ffchain5": synth.FFCHAIN5,
+}
+
+
+def _weakly_connected(vertices, arcs):
+    vertices = set(vertices)
+    if not vertices:
+        return True
+    seen, todo = set(), [min(vertices)]
+    while todo:
+        v = todo.pop()
+        if v in seen:
+            continue
+        seen.add(v)
+        todo += [b for a, b in arcs if a == v and b in vertices] + [a for a, b in arcs if b == v and a in vertices]
+    return seen == vertices
+
+
+def test_product_choices():
+    P = PRODUCT_PATTERNS
+    expect = {"star4": (2, 2, xm.XM_PROD_CHOOSE), "star5": (2, 3, xm.XM_PROD_CHOOSE),
+              "path4": (2, 2, xm.XM_PROD_IE), "ffchain5": (3, 2, xm.XM_PROD_IE),
+              "mixstar": (2, 2, xm.XM_PROD_CHOOSE)}
+    for name, (level, r, kind) in expect.items():
+        pr = xm.Plan(P[name]).product()
+        assert (pr["level"], pr["r"], pr["kind"]) == (level, r, kind), name
+        assert len(pr["sets"]) == (1 if kind == xm.XM_PROD_CHOOSE else 2 ** r - 1)
+    # every vertex of the 4-cycle, bi-fan and bi-parallel pattern has a
+    # neighbour on each side: removing two non-adjacent ones disconnects
+    for pat in (synth.CYCLE4, synth.BIFAN, synth.BIPARALLEL, synth.CYCLE3, synth.FFL):
+        assert xm.Plan(pat).product()["r"] == 0
+    for flags in (xm.XM_NO_PRODUCT, xm.XM_INDUCED):
+        assert xm.Plan(P["star4"], flags).product()["r"] == 0
+    assert "product: level 2 r=3 kind=choose" in xm.Plan(P["star5"]).describe()
+
+
+@pytest.mark.parametrize("pattern", list(PRODUCT_PATTERNS.values()) + random_patterns(24, 31))
+def test_product_structure(pattern):
+    k, arcs = pattern
+    aset = set(arcs)
+    for flags in (xm.XM_REDUCE, xm.XM_NO_REDUCE, xm.XM_EMBEDDINGS):
+        p = xm.Plan(pattern, flags)
+        pr = p.product()
+        if pr["r"] == 0:
+            assert pr["sets"] == []
+            continue
+        order, lvl, r = p.order(), pr["level"], pr["r"]
+        assert lvl == k - r and lvl >= 2 and order[0] == p.start
+        tail = order[lvl:]
+        # the product vertices share no arc, the rest stays connected
+        assert not any((a, b) in aset for a in tail for b in tail)
+        assert _weakly_connected(order[:lvl], arcs)
+        prefix = (1 << lvl) - 1
+        for i, S in enumerate(pr["sets"]):
+            members = [lvl + j for j in range(r) if (i + 1) >> j & 1] if pr["kind"] == xm.XM_PROD_IE else [lvl]
+            want = sorted({op for m in members for op in p.level(m)["ops"]})
+            assert S["vertex"] == -1 and sorted(S["ops"]) == want
+            assert all(j < lvl for j, _ in S["ops"])
+            assert (S["lo_mask"] | S["hi_mask"] | S["neq_mask"]) & ~prefix == 0
+            assert S["dout_min"] == 0 and S["din_min"] == 0 and S["diffs"] == []
+            if S["reuse"] >= 0:
+                assert 1 <= S["reuse"] < lvl
+                assert set(p.level(S["reuse"])["ops"]) <= set(S["ops"])
+        if flags & xm.XM_EMBEDDINGS:
+            assert pr["kind"] == xm.XM_PROD_IE
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+@pytest.mark.parametrize("name", sorted(PRODUCT_PATTERNS))
+def test_product_plans_vs_oracle(seed, name):
+    """The product sets, counted by brute force over distinct tuples by the
+    plan interpreter, give the oracle's counts."""
+    pattern = PRODUCT_PATTERNS[name]
+    n, src, dst = synth.er_graph(12, 60, seed=seed)
+    out, inn = adjacency_lists(n, src, dst)
+    g = oracle.OracleGraph(n, src, dst)
+    for flags in (xm.XM_REDUCE, xm.XM_NO_REDUCE):
+        p = xm.Plan(pattern, flags)
+        assert p.product()["r"] > 0
+        assert run_plan(n, out, inn, p) == g.count_matches(pattern)
+        assert run_plan(n, out, inn, p, use_product=False) == g.count_matches(pattern)
+    pe = xm.Plan(pattern, xm.XM_EMBEDDINGS)
+    assert run_plan(n, out, inn, pe) == g.count_embeddings(pattern)

@@ -364,3 +364,97 @@ def test_plan_autotuner(xm, rmat_small):
     assert ms > 0 and tuple(best.values()) in cands
     assert p.tuning() == best
     assert xm.xm_count(g, p) == want
+
+
+# ------------------------------------------------ leaf products (Sec. 5.3)
+
+PRODUCT_PATTERNS = {
+    "star4": (4, [(0, 1), (0, 2), (0, 3)]),
+    "instar4": (4, [(1, 0), (2, 0), (3, 0)]),
+    "path4": (4, [(0, 1), (1, 2), (2, 3)]),
+    "mixstar": (4, [(0, 1), (2, 0), (0, 3)]),
+    "star5": (5, [(0, 1), (0, 2), (0, 3), (0, 4)]),
+    "tri_tail": (5, [(0, 1), (1, 2), (0, 2), (2, 3), (2, 4)]),
+    "recip_star": (5, [(0, 1), (1, 0), (0, 2), (2, 0), (0, 3), (0, 4)]),
+    "fan3": (5, [(0, 1), (0, 2), (0, 3), (4, 1), (4, 2), (4, 3)]),
+    "path5": (5, [(0, 1), (1, 2), (2, 3), (3, 4)]),
+    "ffchain5": synth.FFCHAIN5,
+}
+
+
+@pytest.mark.parametrize("name", sorted(PRODUCT_PATTERNS))
+def test_products_tiny(xm, tiny, name):
+    """Counting with a leaf product (choose or inclusion-exclusion) equals
+    the oracle and the plain level-by-level walk, in every plan variant."""
+    g, og = tiny
+    pat = PRODUCT_PATTERNS[name]
+    want = og.count_matches(pat)
+    assert xm.Plan(pat).product()["r"] > 0
+    for flags in (xm.XM_REDUCE, xm.XM_NO_REDUCE, xm.XM_NO_PRODUCT):
+        for tun in TUNINGS:
+            p = xm.Plan(pat, flags)
+            p.set_tuning(**tun)
+            assert xm.xm_count(g, p) == want, (flags, tun)
+    assert xm.xm_count(g, xm.Plan(pat, xm.XM_EMBEDDINGS)) == og.count_embeddings(pat)
+
+
+@pytest.mark.parametrize("name", ["star4", "instar4", "path4", "mixstar", "tri_tail", "recip_star", "fan3",
+                                  "path5", "ffchain5"])
+def test_products_rmat(xm, rmat_tiny, name):
+    g, og = rmat_tiny
+    pat = PRODUCT_PATTERNS[name]
+    want = og.count_matches(pat)
+    for tun in (TUNINGS[0], TUNINGS[2]):
+        p = xm.Plan(pat)
+        p.set_tuning(**tun)
+        assert xm.xm_count(g, p) == want, tun
+    assert xm.xm_count(g, xm.Plan(pat, xm.XM_NO_PRODUCT)) == want
+    c, st = xm.xm_count_stats(g, xm.Plan(pat))
+    assert c == want and st["alg_bytes"] > 0
+
+
+def test_products_root_ranges_and_enumeration(xm, tiny, rmat_tiny):
+    g, og = rmat_tiny
+    for name in ("path4", "mixstar", "ffchain5"):
+        pat = PRODUCT_PATTERNS[name]
+        p = xm.Plan(pat)
+        whole = xm.xm_count(g, p)
+        cuts = [0, 1, 3, 100, 257, g.n]
+        assert sum(xm.xm_count_range(g, p, a, b) for a, b in zip(cuts, cuts[1:])) == whole
+        pe = xm.Plan(pat, xm.XM_EMBEDDINGS)
+        for r in (0, 1, 7, 300):
+            assert xm.xm_count_range(g, pe, r, r + 1) == og.count_embeddings(pat, pe.start, r, r + 1)
+    # enumeration walks every level; the plan's reordered vertices still
+    # land in pattern-vertex order
+    g, og = tiny
+    for name in ("path4", "tri_tail", "star4"):
+        pat = PRODUCT_PATTERNS[name]
+        want = og.count_matches(pat)
+        p = xm.Plan(pat)
+        out = torch.full((max(want, 1) * pat[0],), -1, dtype=torch.int32, device="cuda")
+        total, written, over = xm.xm_enumerate(g, p, out)
+        assert total == want and written == want and not over
+        rows = oracle.canonicalize(pat, out[: want * pat[0]].view(-1, pat[0]).cpu().numpy())
+        assert np.array_equal(rows, og.enumerate(pat))
+
+
+def test_product_stars_s20_beyond_64_bits(xm, s20):
+    """Out- and in-stars at full size against exact closed forms: a star with
+    r leaves has sum_v C(outdeg(v), r) matches. The six-leaf out-star sums
+    past 2^64, through the 128-bit product path."""
+    from math import comb
+    g, og = s20
+    off, adj = og.out_csr()
+    outdeg = np.diff(off)
+    indeg = np.bincount(adj, minlength=og.n)
+    for r, deg, inward in ((3, outdeg, False), (4, indeg, True), (6, outdeg, False)):
+        arcs = [(i, 0) for i in range(1, r + 1)] if inward else [(0, i) for i in range(1, r + 1)]
+        pat = (r + 1, arcs)
+        p = xm.Plan(pat)
+        assert p.product()["kind"] == xm.XM_PROD_CHOOSE
+        vals, cnts = np.unique(deg, return_counts=True)
+        want = sum(comb(int(d), r) * int(c) for d, c in zip(vals, cnts))
+        got = xm.xm_count(g, p)
+        assert got == want, r
+        if r == 6:
+            assert want > 2 ** 64
