@@ -61,7 +61,8 @@ enum {
     XM_INDUCED = 4,    /* induced matching: a pair of pattern vertices without an arc must map to a
                           pair of nodes without that arc (DIFF operands); the paper defines only
                           edge and degree constraints, so this is an extension */
-    XM_NO_PRODUCT = 8  /* count by walking every level: no leaf products (see xm_plan_product) */
+    XM_NO_PRODUCT = 8, /* count by walking every level: no leaf products (see xm_plan_product) */
+    XM_NO_SPLIT = 16   /* count with the whole pattern: no cut-vertex decomposition (see xm_plan_split) */
 };
 
 typedef struct xm_graph_s *xm_graph;
@@ -140,7 +141,7 @@ void xm_graph_free(xm_graph g);
  *   e          pattern arcs, 1 <= e <= k(k-1).
  *   psrc, pdst arc endpoints (host memory), e int32 each.
  *   flags      XM_REDUCE (0) | XM_NO_REDUCE | XM_EMBEDDINGS | XM_INDUCED |
- *              XM_NO_PRODUCT.
+ *              XM_NO_PRODUCT | XM_NO_SPLIT.
  *   out        receives the plan handle.
  * Errors: XM_EINVAL for a self-loop, a repeated arc, an id outside [0, k),
  * k or e out of range, or a pattern that is not weakly connected.
@@ -239,6 +240,55 @@ int xm_plan_product(xm_plan p, int32_t *level, int32_t *r, int32_t *kind, int32_
  * Errors: XM_EINVAL for a NULL plan or i outside [0, n_sets).
  */
 int xm_plan_product_set(xm_plan p, int32_t i, xm_level_info *out);
+
+/*
+ * xm_plan_split -- the plan's cut-vertex decomposition, used by xm_count.
+ *
+ * When the pattern has a cut vertex c (a vertex whose removal splits it into
+ * parts A_1..A_t, t >= 2) and the plan would walk three or more levels,
+ * xm_count counts with the parts instead of the whole pattern: for each
+ * node v the embeddings of every A_i + c that map c to v are counted
+ * (rooted plans, one launch per part), their products are summed over v
+ * (one more kernel), and the embeddings of the quotient patterns -- the
+ * pattern with vertices of different parts identified, which the products
+ * also count -- are subtracted (each counted by its own plan, recursively).
+ * This extends the paper's count-by-multiplication (Sec. 5.3) from single
+ * vertices to whole parts; the subtraction keeps matches injective. Cut
+ * vertex choice: most parts, then the smallest largest part, then the
+ * lowest id. Not with XM_INDUCED or XM_NO_SPLIT, nor when a leaf product
+ * already stops the walk at level 2, nor beyond 4096 quotient partitions.
+ * xm_count_range, xm_count_roots, xm_count_stats, the enumerations, batches,
+ * the server and xm_count_noalloc always walk the plan itself.
+ *
+ *   cut          the cut vertex, or -1 when the plan has no decomposition;
+ *   n_parts      t;  n_quotients  distinct quotient patterns (up to
+ *                isomorphism);
+ *   part_factor  product over the parts of the automorphisms of A_i + c
+ *                that fix c (rooted plans count one embedding per orbit).
+ * Any pointer may be NULL. Errors: XM_EINVAL for a NULL plan.
+ */
+int xm_plan_split(xm_plan p, int32_t *cut, int32_t *n_parts, int32_t *n_quotients, int64_t *part_factor);
+
+/*
+ * xm_plan_split_part -- part i of the decomposition as a pattern A_i + c
+ * with its vertices relabelled 0..k-1, c being 0: k, e arcs psrc/pdst
+ * (caller arrays of >= 56 entries), vertices[j] = the original pattern
+ * vertex of label j (>= 8 entries), stab = automorphisms of A_i + c fixing
+ * c. Any output pointer may be NULL.
+ * Errors: XM_EINVAL for a NULL plan, no decomposition or i out of range.
+ */
+int xm_plan_split_part(xm_plan p, int32_t i, int32_t *k, int32_t *e, int32_t *psrc, int32_t *pdst,
+                       int32_t *vertices, int32_t *stab);
+
+/*
+ * xm_plan_split_quotient -- quotient pattern i (k vertices, e arcs into
+ * caller arrays of >= 56 entries; the cut vertex is 0) and mult, the number
+ * of identifications of vertices across parts that yield it. Any output
+ * pointer may be NULL.
+ * Errors: XM_EINVAL for a NULL plan, no decomposition or i out of range.
+ */
+int xm_plan_split_quotient(xm_plan p, int32_t i, int32_t *k, int32_t *e, int32_t *psrc, int32_t *pdst,
+                           int64_t *mult);
 
 /* Frees a plan. NULL is a no-op. */
 void xm_plan_free(xm_plan p);

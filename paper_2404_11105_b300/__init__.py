@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libxm.so")
 
 XM_OK, XM_EINVAL, XM_ENOMEM, XM_EOVERFLOW, XM_ECUDA, XM_ETIMEOUT, XM_EBUSY = range(7)
-XM_REDUCE, XM_NO_REDUCE, XM_EMBEDDINGS, XM_INDUCED, XM_NO_PRODUCT = 0, 1, 2, 4, 8
+XM_REDUCE, XM_NO_REDUCE, XM_EMBEDDINGS, XM_INDUCED, XM_NO_PRODUCT, XM_NO_SPLIT = 0, 1, 2, 4, 8, 16
 XM_PROD_NONE, XM_PROD_CHOOSE, XM_PROD_IE = 0, 1, 2
 
 # every symbol include/xm.h declares
@@ -31,7 +31,8 @@ EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_gr
            "xm_batch_run_graph", "xm_batch_counts", "xm_batch_tune", "xm_batch_free", "xm_count_batch",
            "xm_query_bytes", "xm_server_create", "xm_server_submit", "xm_server_poll", "xm_server_info",
            "xm_server_free", "xm_count_roots", "xm_enumerate_roots", "xm_count_roots_stats", "xm_plan_tune",
-           "xm_plan_product", "xm_plan_product_set"]
+           "xm_plan_product", "xm_plan_product_set", "xm_plan_split", "xm_plan_split_part",
+           "xm_plan_split_quotient"]
 
 
 class XmError(RuntimeError):
@@ -78,6 +79,9 @@ def _load():
         "xm_plan_level": (ctypes.c_int, [vp, i32, ctypes.POINTER(xm_level_info)]),
         "xm_plan_product": (ctypes.c_int, [vp, i32p, i32p, i32p, i32p]),
         "xm_plan_product_set": (ctypes.c_int, [vp, i32, ctypes.POINTER(xm_level_info)]),
+        "xm_plan_split": (ctypes.c_int, [vp, i32p, i32p, i32p, ctypes.POINTER(i64)]),
+        "xm_plan_split_part": (ctypes.c_int, [vp, i32, i32p, i32p, i32p, i32p, i32p, i32p]),
+        "xm_plan_split_quotient": (ctypes.c_int, [vp, i32, i32p, i32p, i32p, i32p, ctypes.POINTER(i64)]),
         "xm_plan_describe": (ctypes.c_int, [vp, ctypes.c_char_p, i32]),
         "xm_plan_free": (None, [vp]),
         "xm_plan_set_tuning": (ctypes.c_int, [vp, ctypes.POINTER(xm_tuning)]),
@@ -238,6 +242,31 @@ class Plan:
             _check(lib().xm_plan_product_set(self._h, i, ctypes.byref(info)))
             sets.append(self._level_dict(info))
         return {"level": level, "r": r, "kind": kind, "sets": sets}
+
+    def split(self) -> dict:
+        """Cut-vertex decomposition used by xm_count: the cut vertex (-1:
+        none), the parts as rooted patterns (root 0) with their vertices in
+        the original pattern and stabiliser sizes, and the quotient patterns
+        with multiplicities."""
+        cut, npart, nquot = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        factor = ctypes.c_int64()
+        _check(lib().xm_plan_split(self._h, ctypes.byref(cut), ctypes.byref(npart), ctypes.byref(nquot),
+                                   ctypes.byref(factor)))
+        parts, quots = [], []
+        for i in range(npart.value):
+            k, e, stab = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+            ps, pd, vs = (ctypes.c_int32 * 56)(), (ctypes.c_int32 * 56)(), (ctypes.c_int32 * 8)()
+            _check(lib().xm_plan_split_part(self._h, i, ctypes.byref(k), ctypes.byref(e), ps, pd, vs,
+                                            ctypes.byref(stab)))
+            parts.append({"pattern": (k.value, [(ps[a], pd[a]) for a in range(e.value)]),
+                          "vertices": list(vs[: k.value]), "stab": stab.value})
+        for i in range(nquot.value):
+            k, e, mult = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+            ps, pd = (ctypes.c_int32 * 56)(), (ctypes.c_int32 * 56)()
+            _check(lib().xm_plan_split_quotient(self._h, i, ctypes.byref(k), ctypes.byref(e), ps, pd,
+                                                ctypes.byref(mult)))
+            quots.append({"pattern": (k.value, [(ps[a], pd[a]) for a in range(e.value)]), "mult": mult.value})
+        return {"cut": cut.value, "parts": parts, "part_factor": factor.value, "quotients": quots}
 
     def describe(self) -> str:
         need = lib().xm_plan_describe(self._h, None, 0)

@@ -375,6 +375,48 @@ int xm_plan_product_set(xm_plan p, int32_t i, xm_level_info* out) {
     return XM_OK;
 }
 
+int xm_plan_split(xm_plan p, int32_t* cut, int32_t* n_parts, int32_t* n_quotients, int64_t* part_factor) {
+    if (!p) { set_error("NULL plan"); return XM_EINVAL; }
+    const Decomp* d = p->plan.decomp.get();
+    if (cut) *cut = d ? d->cut : -1;
+    if (n_parts) *n_parts = d ? (int32_t)d->parts.size() : 0;
+    if (n_quotients) *n_quotients = d ? (int32_t)d->quots.size() : 0;
+    if (part_factor) *part_factor = d ? d->part_factor : 1;
+    return XM_OK;
+}
+
+static void pattern_out(const Plan& q, int32_t* k, int32_t* e, int32_t* psrc, int32_t* pdst) {
+    if (k) *k = q.k;
+    if (e) *e = q.e;
+    for (int a = 0; a < q.e; a++) {
+        if (psrc) psrc[a] = q.psrc[a];
+        if (pdst) pdst[a] = q.pdst[a];
+    }
+}
+
+int xm_plan_split_part(xm_plan p, int32_t i, int32_t* k, int32_t* e, int32_t* psrc, int32_t* pdst,
+                       int32_t* vertices, int32_t* stab) {
+    if (!p) { set_error("NULL plan"); return XM_EINVAL; }
+    const Decomp* d = p->plan.decomp.get();
+    if (!d || i < 0 || i >= (int32_t)d->parts.size()) { set_error("no such part"); return XM_EINVAL; }
+    const Plan& q = d->parts[i];
+    pattern_out(q, k, e, psrc, pdst);
+    if (vertices)
+        for (size_t j = 0; j < d->part_vertices[i].size(); j++) vertices[j] = d->part_vertices[i][j];
+    if (stab) *stab = q.stab_size;
+    return XM_OK;
+}
+
+int xm_plan_split_quotient(xm_plan p, int32_t i, int32_t* k, int32_t* e, int32_t* psrc, int32_t* pdst,
+                           int64_t* mult) {
+    if (!p) { set_error("NULL plan"); return XM_EINVAL; }
+    const Decomp* d = p->plan.decomp.get();
+    if (!d || i < 0 || i >= (int32_t)d->quots.size()) { set_error("no such quotient"); return XM_EINVAL; }
+    pattern_out(d->quots[i], k, e, psrc, pdst);
+    if (mult) *mult = d->quot_mult[i];
+    return XM_OK;
+}
+
 int xm_plan_describe(xm_plan p, char* buf, int32_t cap) {
     if (!p) { set_error("NULL plan"); return -XM_EINVAL; }
     std::string s = describe_plan(p->plan);

@@ -162,10 +162,11 @@ struct Reducer {
         }
     }
 
-    void run() {
+    void run(int forced_start = -1) {
         int start = 0;
         for (int v = 1; v < P.k; v++)
             if (P.deg[v] > P.deg[start]) start = v;  // maxDegree, ties: lowest id
+        if (forced_start >= 0) start = forced_start;  // rooted plans start at their root
         R.start = start;
         search_split(start);
         while (unvisited) {
@@ -369,16 +370,163 @@ ProductChoice choose_product(const Pat& P, const std::vector<int>& base, const s
     return best;
 }
 
+// ------------------------------------------------- cut-vertex decomposition
+
+// Weakly connected parts of the pattern without vertex c (vertex masks).
+std::vector<uint32_t> parts_without(const Pat& P, int c) {
+    uint32_t left = ((1u << P.k) - 1) & ~(1u << c);
+    std::vector<uint32_t> parts;
+    while (left) {
+        uint32_t comp = left & (~left + 1), frontier = comp;
+        while (frontier) {
+            uint32_t nxt = 0;
+            for (int v = 0; v < P.k; v++)
+                if (frontier >> v & 1u) nxt |= P.outb[v] | P.inb[v];
+            nxt &= left & ~comp;
+            comp |= nxt;
+            frontier = nxt;
+        }
+        parts.push_back(comp);
+        left &= ~comp;
+    }
+    return parts;
+}
+
+// Isomorphism-invariant key of a pattern on k <= 8 vertices: the smallest
+// 64-bit adjacency matrix over all relabellings.
+uint64_t canonical_key(int k, const std::vector<std::pair<int, int>>& arcs) {
+    std::vector<int> p(k);
+    for (int i = 0; i < k; i++) p[i] = i;
+    uint64_t best = ~0ull;
+    do {
+        uint64_t key = 0;
+        for (auto& a : arcs) key |= 1ull << (p[a.first] * 8 + p[a.second]);
+        best = std::min(best, key);
+    } while (std::next_permutation(p.begin(), p.end()));
+    return best;
+}
+
+constexpr int kMaxQuotientPartitions = 4096;
+
+// Picks a cut vertex (most parts, then the smallest largest part, then the
+// lowest id) and builds out.decomp: rooted plans of the parts and the
+// quotient patterns with their multiplicities. Leaves out.decomp null when
+// the pattern has no cut vertex or too many quotients.
+int decompose(const Pat& P, int flags, Plan& out, std::string& err) {
+    const int k = P.k;
+    int cut = -1, best_big = 0;
+    std::vector<uint32_t> best_parts;
+    for (int c = 0; c < k; c++) {
+        std::vector<uint32_t> parts = parts_without(P, c);
+        if (parts.size() < 2) continue;
+        int big = 0;
+        for (uint32_t m : parts) big = std::max(big, __builtin_popcount(m));
+        if (cut < 0 || parts.size() > best_parts.size() || (parts.size() == best_parts.size() && big < best_big)) {
+            cut = c;
+            best_parts = parts;
+            best_big = big;
+        }
+    }
+    if (cut < 0) return XM_OK;
+    const int sub_flags = flags & (XM_NO_REDUCE | XM_NO_PRODUCT | XM_NO_SPLIT);
+    auto d = std::make_shared<Decomp>();
+    d->cut = cut;
+    int part_of[XM_MAXK];
+    for (int v = 0; v < k; v++) part_of[v] = -1;
+    for (size_t i = 0; i < best_parts.size(); i++) {
+        std::vector<int> verts{cut};
+        for (int v = 0; v < k; v++)
+            if (best_parts[i] >> v & 1u) { verts.push_back(v); part_of[v] = (int)i; }
+        int lab[XM_MAXK];
+        for (size_t j = 0; j < verts.size(); j++) lab[verts[j]] = (int)j;
+        const uint32_t mask = best_parts[i] | (1u << cut);
+        std::vector<int32_t> s, t;
+        for (int a = 0; a < P.e; a++)
+            if ((mask >> P.s[a] & 1u) && (mask >> P.d[a] & 1u)) {
+                s.push_back(lab[P.s[a]]);
+                t.push_back(lab[P.d[a]]);
+            }
+        Plan sub;
+        int rc = compile_pattern((int)verts.size(), (int)s.size(), s.data(), t.data(),
+                                 sub_flags | XM_NO_PRODUCT | XM_NO_SPLIT, sub, err, 0);
+        if (rc) return rc;
+        d->part_factor *= sub.stab_size;
+        d->part_vertices.push_back(verts);
+        d->parts.push_back(std::move(sub));
+    }
+    // partitions of V \ {c} whose blocks hold at most one vertex of a part
+    std::vector<int> vs;
+    for (int v = 0; v < k; v++)
+        if (v != cut) vs.push_back(v);
+    std::vector<int> block(vs.size());
+    std::vector<uint32_t> block_parts;
+    std::vector<uint64_t> keys;
+    int n_partitions = 0;
+    bool too_many = false;
+    auto emit = [&]() -> int {
+        if (block_parts.size() == vs.size()) return XM_OK;  // the finest: P itself
+        if (++n_partitions > kMaxQuotientPartitions) { too_many = true; return XM_OK; }
+        int lab[XM_MAXK];
+        lab[cut] = 0;
+        for (size_t i = 0; i < vs.size(); i++) lab[vs[i]] = block[i] + 1;
+        const int qk = (int)block_parts.size() + 1;
+        uint64_t seen = 0;
+        std::vector<std::pair<int, int>> arcs;
+        for (int a = 0; a < P.e; a++) {
+            const int u = lab[P.s[a]], v = lab[P.d[a]];
+            if (seen >> (u * 8 + v) & 1ull) continue;
+            seen |= 1ull << (u * 8 + v);
+            arcs.push_back({u, v});
+        }
+        const uint64_t key = canonical_key(qk, arcs);
+        for (size_t j = 0; j < keys.size(); j++)
+            if (keys[j] == key && d->quots[j].k == qk) { d->quot_mult[j]++; return XM_OK; }
+        std::vector<int32_t> s, t;
+        for (auto& a : arcs) { s.push_back(a.first); t.push_back(a.second); }
+        Plan q;
+        int rc = compile_pattern(qk, (int)s.size(), s.data(), t.data(), sub_flags, q, err);
+        if (rc) return rc;
+        keys.push_back(key);
+        d->quots.push_back(std::move(q));
+        d->quot_mult.push_back(1);
+        return XM_OK;
+    };
+    auto rec = [&](auto&& self, size_t i) -> int {
+        if (too_many) return XM_OK;
+        if (i == vs.size()) return emit();
+        const uint32_t pb = 1u << part_of[vs[i]];
+        for (size_t b = 0; b <= block_parts.size(); b++) {
+            if (b < block_parts.size() && (block_parts[b] & pb)) continue;
+            block[i] = (int)b;
+            const bool fresh = b == block_parts.size();
+            if (fresh) block_parts.push_back(pb); else block_parts[b] |= pb;
+            int rc = self(self, i + 1);
+            if (fresh) block_parts.pop_back(); else block_parts[b] &= ~pb;
+            if (rc) return rc;
+        }
+        return XM_OK;
+    };
+    int rc = rec(rec, 0);
+    if (rc) return rc;
+    if (too_many) return XM_OK;
+    out.decomp = d;
+    return XM_OK;
+}
+
 }  // namespace
 
 // --------------------------------------------------------------- compile ---
 
 int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pdst, int flags, Plan& out,
-                    std::string& err) {
+                    std::string& err, int root) {
     if (k < 2 || k > XM_MAXK) { err = "k must be in [2, 8]"; return XM_EINVAL; }
     if (e < 1 || e > k * (k - 1)) { err = "arc count out of range"; return XM_EINVAL; }
     if (!psrc || !pdst) { err = "NULL arc array"; return XM_EINVAL; }
-    if (flags & ~(XM_NO_REDUCE | XM_EMBEDDINGS | XM_INDUCED | XM_NO_PRODUCT)) { err = "unknown flag"; return XM_EINVAL; }
+    if (flags & ~(XM_NO_REDUCE | XM_EMBEDDINGS | XM_INDUCED | XM_NO_PRODUCT | XM_NO_SPLIT)) {
+        err = "unknown flag";
+        return XM_EINVAL;
+    }
+    if (root >= k) { err = "root out of range"; return XM_EINVAL; }
     Pat P;
     P.k = k;
     P.e = e;
@@ -411,13 +559,18 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
     const bool reduce = !(flags & XM_NO_REDUCE);
     std::vector<std::vector<int>> aut;
     automorphisms(P, aut);
+    // a rooted plan maps the root to a given node: its symmetry conditions
+    // come from the automorphisms that fix the root
+    std::vector<std::vector<int>> sym;
+    for (auto& g : aut)
+        if (root < 0 || g[root] == root) sym.push_back(g);
     std::vector<uint64_t> incl = reduce ? inclusion_sets(P) : std::vector<uint64_t>(e, 0);
     Reducer red(P, incl, reduce);
-    red.run();
+    red.run(root);
     const Reduction& R = red.R;
     std::vector<int> order = materialisation_order(P, R);
     ProductChoice pc;
-    if (!(flags & (XM_INDUCED | XM_NO_PRODUCT)) && k >= 4) {
+    if (!(flags & (XM_INDUCED | XM_NO_PRODUCT)) && k >= 4 && root < 0) {
         pc = choose_product(P, order, aut, !(flags & XM_EMBEDDINGS));
         if (pc.r) order = pc.order;
     }
@@ -426,7 +579,7 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
     if (flags & XM_EMBEDDINGS)
         for (int i = 0; i < k; i++) less[i] = 0;
     else
-        symmetry_conditions(k, order, aut, less);
+        symmetry_conditions(k, order, sym, less);
     // transitive closure of the "<" conditions (used to check reuse bounds)
     uint32_t lt[XM_MAXK];
     for (int i = 0; i < k; i++) lt[i] = less[i];
@@ -648,12 +801,20 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
     out.e = e;
     out.flags = flags;
     out.aut_size = (int)aut.size();
+    out.stab_size = (int)sym.size();
     out.n_reuse = n_reuse;
     out.start = R.start;
     out.split = R.split;
     out.covered_by = R.covered_by;
     out.psrc.assign(psrc, psrc + e);
     out.pdst.assign(pdst, pdst + e);
+    out.decomp.reset();
+    // Counting by a cut vertex, when the plan still walks three or more
+    // levels (a product at level 2 is cheaper than any split).
+    if (root < 0 && k >= 4 && !(flags & (XM_INDUCED | XM_NO_SPLIT)) && (D.prod_r == 0 || D.prod_p >= 3)) {
+        int rc = decompose(P, flags, out, err);
+        if (rc) return rc;
+    }
     return XM_OK;
 }
 

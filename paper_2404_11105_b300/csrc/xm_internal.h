@@ -16,19 +16,40 @@ struct xm_graph_s;
 
 namespace xm {
 
+struct Decomp;
+
 struct Plan {
     XmPlanDev dev;
     int k = 0, e = 0, flags = 0;
     int aut_size = 1;
+    int stab_size = 1;  // rooted plans: automorphisms that fix the root
     int n_reuse = 0;
     int start = 0;
     std::vector<int> split;
     std::vector<int> covered_by;
     std::vector<int32_t> psrc, pdst;
+    std::shared_ptr<Decomp> decomp;  // counting by a cut vertex, or null
+};
+
+// Count by a cut vertex c of the pattern: the pattern minus c falls apart
+// into parts A_1..A_t (each taken with c). A map that is injective on every
+// A_i + c is an embedding of the pattern exactly when no two parts share a
+// node; otherwise the shared nodes identify vertices of different parts (a
+// partition s of V \ {c} whose blocks hold at most one vertex of each part)
+// and the map is an embedding of the quotient pattern P/s. Hence
+//   emb(P) = sum_v prod_i emb_i(v) - sum_{s not finest} emb(P/s),
+// with emb_i(v) the embeddings of A_i + c that map c to node v.
+struct Decomp {
+    int cut = -1;
+    std::vector<std::vector<int>> part_vertices;  // pattern vertices of A_i + c (c first)
+    std::vector<Plan> parts;     // rooted plans of A_i + c (vertices relabelled in that order, root 0)
+    long long part_factor = 1;   // prod_i |Stab(c) in Aut(A_i + c)|: rooted matches -> embeddings
+    std::vector<Plan> quots;     // the quotients P/s, one per isomorphism class
+    std::vector<long long> quot_mult;  // number of partitions s in each class
 };
 
 int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pdst, int flags, Plan& out,
-                    std::string& err);
+                    std::string& err, int root = -1);
 std::string describe_plan(const Plan& p);
 
 // Allocator whose resize() leaves new elements uninitialised (large host

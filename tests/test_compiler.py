@@ -269,3 +269,74 @@ def test_product_plans_vs_oracle(seed, name):
         assert run_plan(n, out, inn, p, use_product=False) == g.count_matches(pattern)
     pe = xm.Plan(pattern, xm.XM_EMBEDDINGS)
     assert run_plan(n, out, inn, pe) == g.count_embeddings(pattern)
+
+
+# ------------------------------------------ cut-vertex decomposition (count)
+
+SPLIT_PATTERNS = {
+    "ffchain5": synth.FFCHAIN5,
+    "path5": (5, [(0, 1), (1, 2), (2, 3), (3, 4)]),
+    "tri_tail": (5, [(0, 1), (1, 2), (0, 2), (2, 3), (2, 4)]),
+    "ffl_tail": (4, [(0, 1), (1, 2), (0, 2), (2, 3)]),
+    "bowtie": (5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2)]),
+    "four_parts": (6, [(0, 1), (1, 0), (0, 2), (2, 3), (3, 0), (4, 0), (0, 5)]),
+    "recip_path": (5, [(0, 1), (1, 0), (1, 2), (2, 3), (3, 2), (3, 4)]),
+}
+
+
+def test_split_choices():
+    sp = xm.Plan(SPLIT_PATTERNS["ffchain5"]).split()
+    assert sp["cut"] == 2 and len(sp["parts"]) == 2 and sp["part_factor"] == 2
+    assert sorted(q["mult"] for q in sp["quotients"]) == [2, 2, 2]
+    assert len(xm.Plan(SPLIT_PATTERNS["four_parts"]).split()["parts"]) == 4
+    # 2-connected patterns and plans a product ends at level 2 do not split
+    for pat in (synth.CYCLE4, synth.BIFAN, synth.BIPARALLEL, (4, [(0, 1), (0, 2), (0, 3)]), synth.CYCLE3):
+        assert xm.Plan(pat).split()["cut"] == -1
+    for flags in (xm.XM_NO_SPLIT, xm.XM_INDUCED):
+        assert xm.Plan(synth.FFCHAIN5, flags).split()["cut"] == -1
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+@pytest.mark.parametrize("name", sorted(SPLIT_PATTERNS))
+def test_split_identity_vs_oracle(seed, name):
+    """The decomposition's parts, stabilisers, quotients and multiplicities,
+    evaluated with the oracle alone: sum over nodes v of the product of the
+    parts' embeddings rooted at v, minus the quotients' embeddings, is the
+    pattern's embedding count."""
+    pattern = SPLIT_PATTERNS[name]
+    k, arcs = pattern
+    n, src, dst = synth.er_graph(11, 70, seed=seed)
+    g = oracle.OracleGraph(n, src, dst)
+    for flags in (xm.XM_REDUCE, xm.XM_NO_REDUCE, xm.XM_EMBEDDINGS, xm.XM_NO_PRODUCT):
+        plan = xm.Plan(pattern, flags)
+        sp = plan.split()
+        if sp["cut"] < 0:
+            # a leaf product that stops the walk at level 2 is kept instead
+            assert plan.product()["level"] == 2 and not flags & xm.XM_NO_PRODUCT, name
+            continue
+        cut = sp["cut"]
+        seen = set()
+        factor = 1
+        for part in sp["parts"]:
+            pk, parcs = part["pattern"]
+            vs = part["vertices"]
+            assert vs[0] == cut and len(vs) == pk
+            assert not (set(vs[1:]) & seen)
+            seen |= set(vs[1:])
+            # the part is the induced sub-pattern on its vertices, relabelled
+            assert sorted((vs[a], vs[b]) for a, b in parcs) == \
+                sorted((a, b) for a, b in arcs if a in vs and b in vs)
+            aut = oracle.automorphisms(part["pattern"])
+            assert part["stab"] == sum(1 for row in aut if row[0] == 0)
+            factor *= part["stab"]
+        assert seen == set(range(k)) - {cut} and sp["part_factor"] == factor
+        total = 0
+        for v in range(n):
+            prod = 1
+            for part in sp["parts"]:
+                prod *= g.count_embeddings(part["pattern"], 0, v, v + 1)
+            total += prod
+        for q in sp["quotients"]:
+            assert q["pattern"][0] < k and q["mult"] >= 1
+            total -= q["mult"] * g.count_embeddings(q["pattern"])
+        assert total == g.count_embeddings(pattern)
