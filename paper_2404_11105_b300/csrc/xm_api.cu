@@ -60,6 +60,7 @@ static void free_graph(xm_graph_s* g) {
     cudaFree(g->d_e_units);
     cudaFree(g->d_block_sums);
     cudaFree(g->d_ctl);
+    cudaFree(g->d_root_counts);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
     delete g;
@@ -72,16 +73,17 @@ static XmPlanDev* ctl_plan(xm_graph_s* g) {
     return reinterpret_cast<XmPlanDev*>(reinterpret_cast<unsigned char*>(g->d_ctl) + CTL_WORDS * sizeof(unsigned long long));
 }
 
-static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int32_t* out, uint64_t capacity,
-               uint64_t* lo, uint64_t* hi, xm_stats* stats, uint64_t* written, cudaStream_t stream,
-               const int32_t* roots = nullptr, int64_t nroots = 0) {
-    if (!g || !p || !lo || !hi) { set_error("NULL argument"); return XM_EINVAL; }
+// One matching pass of plan P over start nodes [r_lo, r_hi) (or the staged
+// root list). With root_counts (count mode) the counts go per start node
+// to root_counts[2 v .. 2 v + 1] instead of *lo, *hi.
+static int run_plan(xm_graph g, const Plan& P, const xm_tuning& t, int mode, int64_t r_lo, int64_t r_hi,
+                    int32_t* out, uint64_t capacity, uint64_t* lo, uint64_t* hi, xm_stats* stats, uint64_t* written,
+                    cudaStream_t stream, const int32_t* roots = nullptr, int64_t nroots = 0,
+                    unsigned long long* root_counts = nullptr) {
     if (mode == MODE_EMIT && capacity > 0 && !out) { set_error("NULL output buffer"); return XM_EINVAL; }
     int cur = -1;
     XM_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
     if (cur != g->device) { set_error("graph lives on another device than the current one"); return XM_EINVAL; }
-    const xm::Plan& P = p->plan;
-    const xm_tuning& t = p->tuning;
     r_lo = std::max<int64_t>(r_lo, 0);
     r_hi = std::min<int64_t>(r_hi, g->n);
     RunArgs a;
@@ -109,6 +111,7 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
     a.out = out;
     a.capacity = capacity;
     a.budget_ns = (unsigned long long)t.budget_ms * 1000000ull;
+    a.root_counts = root_counts;
     XM_CUDA(cudaMemsetAsync(g->d_ctl, 0, CTL_WORDS * sizeof(unsigned long long), stream), "cudaMemsetAsync");
     XM_CUDA(cudaMemcpyAsync(ctl_plan(g), &P.dev, sizeof(XmPlanDev), cudaMemcpyHostToDevice, stream),
             "plan upload");
@@ -142,6 +145,64 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
         set_error("enumeration buffer too small");
         return XM_EOVERFLOW;
     }
+    return XM_OK;
+}
+
+static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int32_t* out, uint64_t capacity,
+               uint64_t* lo, uint64_t* hi, xm_stats* stats, uint64_t* written, cudaStream_t stream,
+               const int32_t* roots = nullptr, int64_t nroots = 0) {
+    if (!g || !p || !lo || !hi) { set_error("NULL argument"); return XM_EINVAL; }
+    return run_plan(g, p->plan, p->tuning, mode, r_lo, r_hi, out, capacity, lo, hi, stats, written, stream, roots,
+                    nroots);
+}
+
+typedef unsigned __int128 u128;
+
+// Whole-graph count of plan P (matches, or embeddings with XM_EMBEDDINGS),
+// through its cut-vertex decomposition when it has one:
+//   emb(P) = part_factor * sum_v prod_i m_i(v) - sum_j mult_j * emb(Q_j)
+// with m_i(v) the rooted matches of part i at node v and Q_j the quotient
+// patterns (counted the same way, recursively).
+static int count_plan(xm_graph g, const Plan& P, const xm_tuning& t, u128& result, cudaStream_t stream) {
+    const Decomp* d = P.decomp.get();
+    if (!d) {
+        uint64_t lo = 0, hi = 0;
+        int rc = run_plan(g, P, t, MODE_COUNT, 0, INT32_MAX, nullptr, 0, &lo, &hi, nullptr, nullptr, stream);
+        result = ((u128)hi << 64) | lo;
+        return rc;
+    }
+    const int nparts = (int)d->parts.size();
+    const size_t words = (size_t)nparts * 2 * (size_t)g->n + 2;
+    if (g->root_count_words < words) {
+        cudaFree(g->d_root_counts);
+        g->d_root_counts = nullptr;
+        g->root_count_words = 0;
+        XM_CUDA(cudaMalloc(&g->d_root_counts, words * sizeof(unsigned long long)), "per-node counters");
+        g->root_count_words = words;
+    }
+    unsigned long long* cnt = g->d_root_counts;
+    unsigned long long* sum = cnt + (size_t)nparts * 2 * g->n;
+    XM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)nparts * 2 * g->n * sizeof(unsigned long long), stream), "memset");
+    for (int i = 0; i < nparts; i++) {
+        uint64_t lo = 0, hi = 0;
+        int rc = run_plan(g, d->parts[i], t, MODE_COUNT, 0, INT32_MAX, nullptr, 0, &lo, &hi, nullptr, nullptr, stream,
+                          nullptr, 0, cnt + (size_t)i * 2 * g->n);
+        if (rc) return rc;
+    }
+    cudaError_t e = launch_root_product(cnt, nparts, g->n, sum, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "part products");
+    unsigned long long s2[2];
+    XM_CUDA(cudaMemcpyAsync(s2, sum, sizeof s2, cudaMemcpyDeviceToHost, stream), "product readback");
+    XM_CUDA(cudaStreamSynchronize(stream), "part products");
+    u128 emb = (((u128)s2[1] << 64) | s2[0]) * (u128)d->part_factor;
+    for (size_t j = 0; j < d->quots.size(); j++) {
+        u128 q = 0;
+        int rc = count_plan(g, d->quots[j], t, q, stream);
+        if (rc) return rc;
+        // quotient plans count matches: embeddings = matches x |Aut(Q)|
+        emb -= q * (u128)d->quots[j].aut_size * (u128)d->quot_mult[j];
+    }
+    result = (P.flags & XM_EMBEDDINGS) ? emb : emb / (u128)P.aut_size;
     return XM_OK;
 }
 
@@ -488,7 +549,13 @@ int xm_plan_tune(xm_graph g, xm_plan p, const xm_tuning* cand, int32_t ncand, in
 }
 
 int xm_count(xm_graph g, xm_plan p, uint64_t* lo, uint64_t* hi, void* stream) {
-    return run(g, p, MODE_COUNT, 0, INT32_MAX, nullptr, 0, lo, hi, nullptr, nullptr, (cudaStream_t)stream);
+    if (!g || !p || !lo || !hi) { set_error("NULL argument"); return XM_EINVAL; }
+    u128 r = 0;
+    int rc = count_plan(g, p->plan, p->tuning, r, (cudaStream_t)stream);
+    if (rc) return rc;
+    *lo = (uint64_t)r;
+    *hi = (uint64_t)(r >> 64);
+    return XM_OK;
 }
 
 int xm_count_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t* lo, uint64_t* hi,

@@ -104,6 +104,8 @@ struct xm_graph_s {
     // chunk counts and offsets, first-level candidate sets, work units, scan
     // partials, and a small control block (counters, accumulators, plan)
     int32_t* d_roots = nullptr;        // n: explicit start nodes (allocated on first use)
+    unsigned long long* d_root_counts = nullptr;  // per-node part counters of split counts (on first use)
+    size_t root_count_words = 0;
     int32_t* d_root_chunks = nullptr;  // n + 1
     int32_t* d_chunk_cnt = nullptr;    // cmax + 1
     int32_t* d_l1set = nullptr;        // max(m, 1)

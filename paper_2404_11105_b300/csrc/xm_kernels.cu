@@ -940,7 +940,9 @@ __device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDe
     return acc;
 }
 
-template <int MODE, bool PROD>
+// ROOTS (count mode, no product): the count of every unit goes to the
+// 128-bit counter of its start node, ra.root_counts[2 v .. 2 v + 1].
+template <int MODE, bool PROD, bool ROOTS = false>
 __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     extern __shared__ __align__(16) unsigned char smem[];
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(smem);
@@ -972,6 +974,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
     Budget budget;
     budget.start(ra.ctl, ra.budget_ns, lane);
     int owner = -1;
+    int acc_root = -1;  // ROOTS: start-node index the running count belongs to
     for (;;) {
         long long start;
         int cnt;
@@ -992,6 +995,14 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                 owner = found ? o : owner_of(uprefix, nidx, u);
             }
             const int chunk = u - __ldg(uprefix + owner);
+            if (ROOTS) {
+                const int rt = two_level ? owner : __ldg(ra.l1root + owner);
+                if (rt != acc_root) {
+                    if (acc_root >= 0) flush_count(acc, ra.root_counts + 2 * (size_t)root_node(ra, acc_root), lane);
+                    acc = 0;
+                    acc_root = rt;
+                }
+            }
             if (MODE == MODE_STATS && lane == 0) st.units++;
             if (two_level && ke > 2) {
                 // unit = (start node, a piece of its first-level set)
@@ -1100,7 +1111,11 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
         }
         if (stop) break;
     }
-    flush_count(acc, ra.ctl + CTL_COUNT_LO, lane);
+    if (ROOTS) {
+        if (acc_root >= 0) flush_count(acc, ra.root_counts + 2 * (size_t)root_node(ra, acc_root), lane);
+    } else {
+        flush_count(acc, ra.ctl + CTL_COUNT_LO, lane);
+    }
     if (MODE == MODE_STATS && lane == 0) {
         atomicAdd(ra.ctl + CTL_STATS + 0, st.bytes);
         atomicAdd(ra.ctl + CTL_STATS + 1, st.ext);
@@ -1184,6 +1199,35 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
         }
     }
     if (cur >= 0) flush_count(acc, b.counts + 2 * (size_t)cur, lane);
+}
+
+// ------------------------------------------------------ cut-vertex split
+// sum over nodes v of prod_{i < t} cnt_i(v), mod 2^128, where cnt_i(v) is
+// the 128-bit counter cnt[i * 2n + 2v .. + 1]; added to out[0..1].
+__global__ void k_root_product(const unsigned long long* __restrict__ cnt, int t, int n, unsigned long long* out) {
+    typedef unsigned __int128 u128;
+    u128 sum = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        u128 prod = 1;
+        for (int i = 0; i < t && prod; i++) {
+            const unsigned long long* c = cnt + (size_t)i * 2 * n + 2 * (size_t)v;
+            prod *= ((u128)__ldg(c + 1) << 64) | __ldg(c);
+        }
+        sum += prod;
+    }
+    unsigned long long lo = (unsigned long long)sum, hi = (unsigned long long)(sum >> 64);
+    for (int off = 16; off; off >>= 1) {
+        const unsigned long long olo = __shfl_down_sync(FULL, lo, off);
+        const unsigned long long ohi = __shfl_down_sync(FULL, hi, off);
+        const unsigned long long s = lo + olo;
+        hi += ohi + (s < lo ? 1 : 0);
+        lo = s;
+    }
+    if ((threadIdx.x & 31) == 0 && (lo | hi)) {
+        const unsigned long long old = atomicAdd(out, lo);
+        const unsigned long long carry = (old + lo < old) ? 1 : 0;
+        if (hi + carry) atomicAdd(out + 1, hi + carry);
+    }
 }
 
 // ------------------------------------------------------------------- scan
@@ -1320,6 +1364,18 @@ cudaError_t launch_batch(const BatchDev& b, int warps_per_block, int blocks_per_
     return cudaGetLastError();
 }
 
+cudaError_t launch_root_product(const unsigned long long* cnt, int t, int32_t n, unsigned long long* out,
+                                cudaStream_t stream) {
+    cudaError_t err;
+    int dev = 0, nsm = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), stream)) != cudaSuccess) return err;
+    const int grid = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)nsm * 8);
+    k_root_product<<<std::max(grid, 1), 256, 0, stream>>>(cnt, t, n, out);
+    return cudaGetLastError();
+}
+
 int leaf_closed_form_kind(const XmPlanDev& P) {
     if (P.k != 3) return 0;
     const XmLevel& L = P.lv[2];
@@ -1382,10 +1438,13 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
     // 3. persistent matcher
     const size_t smem = match_smem_bytes(P.k, b.window, warps_per_block);
     const bool prod = b.pv != nullptr;
+    const bool roots = b.root_counts != nullptr;
+    if (roots && (mode != MODE_COUNT || prod)) return cudaErrorInvalidValue;
     const void* fn = mode == MODE_STATS ? (prod ? (const void*)k_match<MODE_STATS, true>
                                                 : (const void*)k_match<MODE_STATS, false>)
                      : mode == MODE_EMIT ? (const void*)k_match<MODE_EMIT, false>
                      : prod              ? (const void*)k_match<MODE_COUNT, true>
+                     : roots             ? (const void*)k_match<MODE_COUNT, false, true>
                                          : (const void*)k_match<MODE_COUNT, false>;
     if ((err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return err;
@@ -1404,6 +1463,8 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
         k_match<MODE_EMIT, false><<<grid, block, smem, stream>>>(plan_dev, b);
     else if (prod)
         k_match<MODE_COUNT, true><<<grid, block, smem, stream>>>(plan_dev, b);
+    else if (roots)
+        k_match<MODE_COUNT, false, true><<<grid, block, smem, stream>>>(plan_dev, b);
     else
         k_match<MODE_COUNT, false><<<grid, block, smem, stream>>>(plan_dev, b);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -91,6 +91,8 @@ struct RunArgs {
     unsigned long long budget_ns;  // matcher time budget (0: none)
     int32_t* out;               // enumeration buffer (k ints per match)
     unsigned long long capacity;
+    unsigned long long* root_counts = nullptr;  // count mode: per-start-node 128-bit counters
+                                                // (2 words per node id), else null
     const XmLevel* pv = nullptr;  // leaf-product sets of the device plan when counting
                                   // with a product (set by launch_match), else null
 };
@@ -139,6 +141,11 @@ bool use_l2_units(const XmPlanDev& P, bool counting);
 // 0, or the closed form that counts a three-vertex plan's last level
 // without an intersection per partial match (RunArgs::leaf_kind).
 int leaf_closed_form_kind(const XmPlanDev& P);
+
+// Enqueues out[0..1] = sum over v < n of prod_{i < t} cnt_i(v) (mod 2^128),
+// cnt_i(v) the 128-bit counter at cnt + i * 2n + 2v.
+cudaError_t launch_root_product(const unsigned long long* cnt, int t, int32_t n, unsigned long long* out,
+                                cudaStream_t stream);
 
 // Enqueues the whole matching pass on `stream`: first-level sets, work
 // units, persistent matcher. `plan_dev` is a device copy of the plan.

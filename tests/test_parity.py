@@ -458,3 +458,32 @@ def test_product_stars_s20_beyond_64_bits(xm, s20):
         assert got == want, r
         if r == 6:
             assert want > 2 ** 64
+
+
+# ------------------------------------------ cut-vertex decomposition (count)
+
+SPLIT_PATTERNS = {
+    "ffchain5": synth.FFCHAIN5,
+    "path5": (5, [(0, 1), (1, 2), (2, 3), (3, 4)]),
+    "tri_tail": (5, [(0, 1), (1, 2), (0, 2), (2, 3), (2, 4)]),
+    "bowtie": (5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2)]),
+    "four_parts": (6, [(0, 1), (1, 0), (0, 2), (2, 3), (3, 0), (4, 0), (0, 5)]),
+    "recip_path": (5, [(0, 1), (1, 0), (1, 2), (2, 3), (3, 2), (3, 4)]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SPLIT_PATTERNS))
+def test_split_counts(xm, tiny, rmat_tiny, name):
+    """xm_count through the cut-vertex decomposition (per-node part counts,
+    product sum, quotient counts) equals the oracle and the whole-pattern
+    walk."""
+    pat = SPLIT_PATTERNS[name]
+    assert xm.Plan(pat).split()["cut"] >= 0
+    for g, og in (tiny, rmat_tiny):
+        want = og.count_matches(pat)
+        for flags in (xm.XM_REDUCE, xm.XM_NO_REDUCE, xm.XM_NO_SPLIT, xm.XM_NO_PRODUCT):
+            for tun in (TUNINGS[0], TUNINGS[1]):
+                p = xm.Plan(pat, flags)
+                p.set_tuning(**tun)
+                assert xm.xm_count(g, p) == want, (flags, tun)
+        assert xm.xm_count(g, xm.Plan(pat, xm.XM_EMBEDDINGS)) == og.count_embeddings(pat)
