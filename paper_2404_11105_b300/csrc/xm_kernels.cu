@@ -234,9 +234,10 @@ __device__ __forceinline__ bool list_has(const ListRef& r, int32_t x) {
     return q < r.len && __ldg(r.p + q) == x;
 }
 
-// Induced plans: x must lie in none of the level's difference lists. Kept out
-// of line so that plans without differences do not pay for its code.
-__device__ __noinline__ bool passes_diffs(const XmLevel& L, const GraphDev& g, const int32_t* m, int32_t x) {
+// Induced plans: x must lie in none of the level's difference lists. Inlined:
+// as an out-of-line call its calling convention cost the matcher's count
+// kernel registers (spills) once the product kernels also called it.
+__device__ __forceinline__ bool passes_diffs(const XmLevel& L, const GraphDev& g, const int32_t* m, int32_t x) {
     for (int i = 0; i < L.ndiff; i++)
         if (list_has(op_list(g, L.diff_dir[i], m[L.diff_level[i]]), x)) return false;
     return true;

@@ -479,7 +479,8 @@ def test_split_counts(xm, tiny, rmat_tiny, name):
     walk."""
     pat = SPLIT_PATTERNS[name]
     assert xm.Plan(pat).split()["cut"] >= 0
-    for g, og in (tiny, rmat_tiny):
+    # the six-vertex pattern takes the oracle minutes on the skewed graph
+    for g, og in ((tiny,) if name == "four_parts" else (tiny, rmat_tiny)):
         want = og.count_matches(pat)
         for flags in (xm.XM_REDUCE, xm.XM_NO_REDUCE, xm.XM_NO_SPLIT, xm.XM_NO_PRODUCT):
             for tun in (TUNINGS[0], TUNINGS[1]):
