@@ -447,6 +447,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the per-pattern autotuner (warm-up phase)")
     ap.add_argument("--ablation", action="store_true",
                     help="also time every pattern with its unreduced plan (no candidate-set reuse)")
+    ap.add_argument("--leaf-products", action="store_true",
+                    help="also count leaf-product and cut-vertex-split patterns on the whole graph, each "
+                         "against the level-by-level walk (budget --walk-budget-ms)")
+    ap.add_argument("--walk-budget-ms", type=int, default=20000)
     ap.add_argument("--enum-capacity", type=int, default=1 << 24,
                     help="rmat24: matches written by the untimed enumeration check")
     args = ap.parse_args()
@@ -597,6 +601,48 @@ def main():
             row["speedup"] = round(row["unreduced"]["ms"] / row["reduced"]["ms"], 3)
             ablation[name] = row
 
+    products = None
+    if args.leaf_products:
+        # whole-graph counts that stop early (Sec. 5.3 products, cut-vertex
+        # splits) against the plain walk of every level; wall time of the
+        # xm_count call (a split runs several launches and host steps)
+        products = {}
+        pats_next = dict(synth.LEAF_PRODUCT_PATTERNS) if args.workload != "rmat24" else {}
+        pats_next.update(synth.SPLIT_PATTERNS if args.workload != "rmat24" else {"ffchain5": synth.FFCHAIN5})
+        for name, pat in pats_next.items():
+            row = {}
+            for label, flags in (("early", xm.XM_REDUCE), ("walk", xm.XM_NO_PRODUCT | xm.XM_NO_SPLIT)):
+                if label == "walk" and args.workload == "rmat24":
+                    continue
+                p = xm.Plan(pat, flags)
+                p.set_tuning(budget_ms=args.walk_budget_ms)
+                best = None
+                for _ in range(1 if label == "walk" else 3):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    try:
+                        c = xm.xm_count(g, p)
+                    except xm.XmError as e:
+                        if e.status != xm.XM_ETIMEOUT:
+                            raise
+                        c = None
+                    torch.cuda.synchronize()
+                    t = (time.perf_counter() - t0) * 1e3
+                    best = t if best is None else min(best, t)
+                    if c is None:
+                        break
+                row[label] = {"count": None if c is None else int(c), "ms": round(best, 2),
+                              "timed_out": c is None}
+            pe = xm.Plan(pat)
+            pr, sp = pe.product(), pe.split()
+            row["product"] = {"level": pr["level"], "r": pr["r"], "kind": pr["kind"]} if pr["r"] else None
+            row["split"] = {"cut": sp["cut"], "parts": len(sp["parts"]), "quotients": len(sp["quotients"])} \
+                if sp["cut"] >= 0 else None
+            if "walk" in row and row["walk"]["count"] is not None:
+                assert row["walk"]["count"] == row["early"]["count"], name
+                row["speedup"] = round(row["walk"]["ms"] / row["early"]["ms"], 2)
+            products[name] = row
+
     enum = None
     if roots is not None and args.enum_capacity > 0:
         # enumeration into a device buffer (untimed): the first pattern
@@ -653,6 +699,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": LAUNCHES_PER_CALL * launches, "clocks": clocks,
             "counts": {k: int(v) for k, v in counts.items()}, "enumeration": enum, "ablation": ablation,
+            "leaf_products": products,
             "autotuned": tuned,
             "device_ms_per_pattern": {k: round(statistics.median(v), 3) for k, v in per_pattern_ms.items()}}
     print(json.dumps(line), flush=True)

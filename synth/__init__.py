@@ -152,6 +152,20 @@ def rmat24():
 TINY_PATTERNS = {"cycle3": CYCLE3, "ffl": FFL, "bifan": BIFAN}
 S24_PATTERNS = {"cycle4": CYCLE4, "bifan": BIFAN, "biparallel": BIPARALLEL, "ffchain5": FFCHAIN5}
 
+# patterns whose counts stop early: leaf products (arc-free trailing
+# vertices) and cut-vertex splits
+LEAF_PRODUCT_PATTERNS = {
+    "out_star4": (4, [(0, 1), (0, 2), (0, 3)]),
+    "path4": (4, [(0, 1), (1, 2), (2, 3)]),
+    "mixed_star4": (4, [(0, 1), (2, 0), (0, 3)]),
+    "out_star5": (5, [(0, 1), (0, 2), (0, 3), (0, 4)]),
+}
+SPLIT_PATTERNS = {
+    "ffchain5": FFCHAIN5,
+    "tri_tail": (5, [(0, 1), (1, 2), (0, 2), (2, 3), (2, 4)]),
+    "bowtie": (5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2)]),
+}
+
 
 # ------------------------------------------------------ batch / serve recipes
 
