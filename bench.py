@@ -560,6 +560,7 @@ def main():
     # roofline of the dominant kernel (the matcher): algorithmic bytes from an
     # instrumented, untimed run; duration from the CUDA events of the timed runs
     alg_bytes = 0
+    extensions = 0
     if not args.no_stats:
         for name, p in plans.items():
             if roots is not None:
@@ -568,6 +569,7 @@ def main():
                 c, st = xm.xm_count_stats(g, p, r_lo, r_hi)
             assert c == counts[name] or world > 1
             alg_bytes += st["alg_bytes"]
+            extensions += st["extensions"]
     launches = len(plans) * args.steps
     avg_kernel_s = sum(kernel_ms) / len(kernel_ms) / 1000.0
     bytes_per_launch = alg_bytes / len(plans)
@@ -576,6 +578,12 @@ def main():
     traffic = profiled_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind,
+                # against the nominal 7.7 TB/s, and DRAM bytes (ncu) per second
+                "frac_of_nominal": achieved / 7700.0,
+                "dram_gbs": None if traffic is None else traffic / avg_kernel_s / 1e9,
+                "dram_frac": None if traffic is None else traffic / avg_kernel_s / 1e9 / peak,
+                # partial matches extended per second of matcher time (instrumented run's count)
+                "extensions_per_s": extensions / (sum(kernel_ms) / args.steps / 1000.0) if extensions else None,
                 "kernel": "k_match (persistent matcher)", "kernel_share_of_step":
                     sum(kernel_ms) / sum(step_ms)}
 
@@ -692,6 +700,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "matches/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "ms_per_step_min_max": [min(step_ms), max(step_ms)],
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": desc, "graph_nodes": g.n, "graph_arcs": g.m, "patterns": len(plans),
                        "matches_per_step": total_matches, "l2": "flushed (512 MB write) between timed steps",
