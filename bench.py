@@ -6,7 +6,7 @@ HBM; one step counts the matches of all 13 weakly connected 3-node directed
 motifs (13 xm_count calls). Metric: matches/s = matches found in the step /
 device time of the step.
 
-    python bench.py [--gpus N --steps K --warmup W] [--workload rmat20|tiny|rmat24]
+    python bench.py [--gpus N --steps K --warmup W] [--workload rmat20|tiny|rmat22|rmat24|dense|batch|serve]
     python bench.py --impl reference ...      # the CPU oracle, bounded sample
 
 Prints one JSON line (rank 0).
@@ -46,6 +46,11 @@ def workload(name):
         n, src, dst = synth.rmat24()
         pats = dict(synth.S24_PATTERNS)
         desc = "R-MAT scale 24 EF16 a=.57 b=.19 c=.19 seed 3; 4-cycle, bi-fan, bi-parallel, 5-vertex FF chain"
+    elif name == "dense":
+        n, src, dst = synth.rmat_graph(16, 8, seed=4)
+        pats = {k: synth.DENSE_PATTERNS[k] for k in ("tt5", "tt6", "fan24")}
+        desc = ("R-MAT scale 16 EF8 a=.57 b=.19 c=.19 seed 4; dense 5-6-vertex patterns: transitive "
+                "tournaments on 5 and 6 vertices, 2x4 bipartite fan")
     elif name == "rmat22":
         n, src, dst = synth.rmat_graph(22, 16, seed=6)
         pats = dict(synth.S24_PATTERNS)
@@ -422,7 +427,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="xm", choices=["xm", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rmat22", "rmat24", "batch", "serve"])
+    ap.add_argument("--workload", default="rmat20",
+                    choices=["rmat20", "tiny", "rmat22", "rmat24", "dense", "batch", "serve"])
     ap.add_argument("--serve-graphs", type=int, default=1000)
     ap.add_argument("--serve-rates", default="100,300,1000,3000,10000")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate")
@@ -596,17 +602,26 @@ def main():
             row = {}
             for label, flags in (("reduced", xm.XM_REDUCE), ("unreduced", xm.XM_NO_REDUCE)):
                 p = xm.Plan(pat, flags)
+                if args.budget_ms:
+                    p.set_tuning(budget_ms=args.budget_ms)
                 ms_ = []
-                for _ in range(3):
-                    c = count_one(p)
-                    ms_.append(sum(g.last_timing()))
+                try:
+                    for _ in range(3):
+                        c = count_one(p)
+                        ms_.append(sum(g.last_timing()))
+                except xm.XmError as e:
+                    if e.status != xm.XM_ETIMEOUT:
+                        raise
+                    row[label] = {"timed_out": True, "budget_ms": args.budget_ms, "reuse_levels": p.n_reuse}
+                    continue
                 assert c == counts[name]
                 if roots is not None:
                     _, st = xm.xm_count_roots_stats(g, p, roots)
                 else:
                     _, st = xm.xm_count_stats(g, p, r_lo, r_hi)
                 row[label] = {"ms": round(min(ms_), 3), "alg_bytes": st["alg_bytes"], "reuse_levels": p.n_reuse}
-            row["speedup"] = round(row["unreduced"]["ms"] / row["reduced"]["ms"], 3)
+            if "ms" in row["unreduced"] and "ms" in row["reduced"]:
+                row["speedup"] = round(row["unreduced"]["ms"] / row["reduced"]["ms"], 3)
             ablation[name] = row
 
     products = None

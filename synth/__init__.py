@@ -160,6 +160,26 @@ LEAF_PRODUCT_PATTERNS = {
     "mixed_star4": (4, [(0, 1), (2, 0), (0, 3)]),
     "out_star5": (5, [(0, 1), (0, 2), (0, 3), (0, 4)]),
 }
+# denser 5-7-vertex patterns with many inclusion relations (the paper's
+# 5-7-vertex patterns are not available): transitive tournaments (every
+# arc i -> j for i < j) and complete bipartite fans (every arc u -> v from
+# the first group to the second)
+def transitive_tournament(k: int):
+    return k, [(i, j) for i in range(k) for j in range(i + 1, k)]
+
+
+def bipartite_fan(a: int, b: int):
+    return a + b, [(i, a + j) for i in range(a) for j in range(b)]
+
+
+DENSE_PATTERNS = {
+    "tt5": transitive_tournament(5),
+    "tt6": transitive_tournament(6),
+    "tt7": transitive_tournament(7),
+    "fan24": bipartite_fan(2, 4),
+    "fan33": bipartite_fan(3, 3),
+}
+
 SPLIT_PATTERNS = {
     "ffchain5": FFCHAIN5,
     "tri_tail": (5, [(0, 1), (1, 2), (0, 2), (2, 3), (2, 4)]),
