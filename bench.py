@@ -456,7 +456,7 @@ def main():
     ap.add_argument("--leaf-products", action="store_true",
                     help="also count leaf-product and cut-vertex-split patterns on the whole graph, each "
                          "against the level-by-level walk (budget --walk-budget-ms)")
-    ap.add_argument("--walk-budget-ms", type=int, default=20000)
+    ap.add_argument("--walk-budget-ms", type=int, default=20000, help="0: skip the walks")
     ap.add_argument("--enum-capacity", type=int, default=1 << 24,
                     help="rmat24: matches written by the untimed enumeration check")
     args = ap.parse_args()
@@ -635,10 +635,10 @@ def main():
         for name, pat in pats_next.items():
             row = {}
             for label, flags in (("early", xm.XM_REDUCE), ("walk", xm.XM_NO_PRODUCT | xm.XM_NO_SPLIT)):
-                if label == "walk" and args.workload == "rmat24":
+                if label == "walk" and (args.workload == "rmat24" or args.walk_budget_ms <= 0):
                     continue
                 p = xm.Plan(pat, flags)
-                p.set_tuning(budget_ms=args.walk_budget_ms)
+                p.set_tuning(budget_ms=max(args.walk_budget_ms, 0))
                 best = None
                 for _ in range(1 if label == "walk" else 3):
                     torch.cuda.synchronize()
