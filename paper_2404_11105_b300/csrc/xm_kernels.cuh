@@ -34,12 +34,14 @@ constexpr int HASH_MIN_LEN = 32;
 constexpr int HASH_BUCKET = 8;
 
 __host__ __device__ __forceinline__ uint32_t hash_bucket(int32_t x, uint32_t nbuckets) {
+    // Fibonacci hashing: the top log2(nbuckets) bits of x * 2^32 / phi,
+    // taken as the high word of (hash * nbuckets) (nbuckets a power of two)
+    const uint32_t h = (uint32_t)x * 2654435769u;
 #ifdef __CUDA_ARCH__
-    const int b = __ffs((int)nbuckets) - 1;
+    return __umulhi(h, nbuckets);
 #else
-    const int b = __builtin_ctz(nbuckets);
+    return (uint32_t)(((uint64_t)h * nbuckets) >> 32);
 #endif
-    return b ? (((uint32_t)x * 2654435769u) >> (32 - b)) : 0u;
 }
 
 // Table size in slots for a list of `len` ids (0: no table): a power of two
