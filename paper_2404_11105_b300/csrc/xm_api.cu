@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -235,7 +236,12 @@ int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, 
     if (flags != 0) { set_error("flags must be 0"); return XM_EINVAL; }
     if (n < 1 || m < 0) { set_error("n must be >= 1 and m >= 0"); return XM_EINVAL; }
     cudaStream_t stream = (cudaStream_t)stream_;
-    std::vector<int32_t> hs, hd;
+    // host arrays of the build, kept between loads like the build's own
+    // staging (fresh pages cost a fault each on first touch); loads take turns
+    static std::mutex load_mu;
+    static HostVec<int32_t> hs, hd;
+    static HostCsr H;
+    std::lock_guard<std::mutex> load_lock(load_mu);
     const int32_t* s = src;
     const int32_t* d = dst;
     try {
@@ -248,7 +254,6 @@ int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, 
             s = hs.data();
             d = hd.data();
         }
-        HostCsr H;
         std::string err;
         int rc = build_host_csr(n, m, s, d, H, err);
         if (rc) { set_error(err); return rc; }

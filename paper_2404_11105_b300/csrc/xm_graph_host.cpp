@@ -6,10 +6,13 @@
 // bucket is sorted as packed 64-bit (source, destination) keys and
 // deduplicated on its own, and the buckets are concatenated. The in-lists
 // are built the same way from the deduplicated arcs with the key halves
-// swapped.
+// swapped. The staging arrays are kept between builds (see Staging): pages
+// that are already mapped cost nothing to reuse, while fresh ones cost a page
+// fault each on first touch, which made up half of a scale-20 build.
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -24,6 +27,21 @@ int n_threads(int64_t work) {
     const unsigned hw = std::thread::hardware_concurrency();
     const int64_t cap = std::min<int64_t>(hw ? hw : 1, 64);
     return (int)std::max<int64_t>(1, std::min<int64_t>(cap, work >> 17));
+}
+
+// Host staging arrays of the CSR build, grown to the largest graph built so
+// far and kept until the process exits (about 16 B per arc plus 12 B per
+// node); builds take turns on them.
+struct Staging {
+    std::mutex mu;
+    HostVec<uint64_t> keys;
+    HostVec<int32_t> cols, deg, row_of;
+    HostVec<int64_t> rstart;
+};
+
+Staging& staging() {
+    static Staging s;
+    return s;
 }
 
 template <class F>
@@ -41,7 +59,8 @@ void parallel_for(int64_t n, int nt, F f) {
 // [0, n): off[n+1], adj[count]. Self-loops are dropped. Returns the number of
 // distinct arcs; above 2^31-1 nothing is filled (int32 offsets).
 template <class KeyOf>
-int64_t build_side(int32_t n, int64_t m, KeyOf key_of, HostVec<int32_t>& off, HostVec<int32_t>& adj) {
+int64_t build_side(int32_t n, int64_t m, KeyOf key_of, HostVec<int32_t>& off, HostVec<int32_t>& adj,
+                   Staging& st) {
     const int nt = n_threads(m);
     // buckets of consecutive rows
     const int64_t nb = std::max<int64_t>(1, std::min<int64_t>({(int64_t)n, 8192, m >> 10}));
@@ -67,7 +86,8 @@ int64_t build_side(int32_t n, int64_t m, KeyOf key_of, HostVec<int32_t>& off, Ho
         }
     }
     bstart[nb] = run;
-    HostVec<uint64_t> keys((size_t)std::max<int64_t>(run, 1));
+    HostVec<uint64_t>& keys = st.keys;
+    keys.resize((size_t)std::max<int64_t>(run, 1));
     parallel_for(m, nt, [&](int t, int64_t lo, int64_t hi) {
         int64_t* s = start.data() + (size_t)t * nb;
         for (int64_t i = lo; i < hi; i++) {
@@ -83,9 +103,12 @@ int64_t build_side(int32_t n, int64_t m, KeyOf key_of, HostVec<int32_t>& off, Ho
         lo = (b * n + nb - 1) / nb;
         hi = ((b + 1) * n + nb - 1) / nb;
     };
-    HostVec<int32_t> cols((size_t)std::max<int64_t>(run, 1));
-    HostVec<int64_t> rstart((size_t)n);
-    HostVec<int32_t> deg((size_t)n);
+    HostVec<int32_t>& cols = st.cols;
+    HostVec<int64_t>& rstart = st.rstart;
+    HostVec<int32_t>& deg = st.deg;
+    cols.resize((size_t)std::max<int64_t>(run, 1));
+    rstart.resize((size_t)n);
+    deg.resize((size_t)n);
     std::vector<int64_t> kept(nb, 0);
     std::atomic<int64_t> next{0};
     auto sort_rows = [&](int, int64_t, int64_t) {
@@ -160,22 +183,25 @@ int build_host_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
     if (bad) { err = "arc endpoint outside [0, n)"; return XM_EINVAL; }
     // the arc count after deduplication must fit the int32 offsets
     if (m > (int64_t)INT32_MAX * 2) { err = "too many arcs"; return XM_EINVAL; }
+    Staging& st = staging();
+    std::lock_guard<std::mutex> lock(st.mu);
 
     const int64_t total = build_side(
-        n, m, [&](int64_t i) { return ((uint64_t)(uint32_t)src[i] << 32) | (uint32_t)dst[i]; }, G.out_off, G.out_adj);
+        n, m, [&](int64_t i) { return ((uint64_t)(uint32_t)src[i] << 32) | (uint32_t)dst[i]; }, G.out_off, G.out_adj, st);
     if (total > INT32_MAX) { err = "more than 2^31-1 arcs after deduplication"; return XM_EINVAL; }
     G.n = n;
     G.m = total;
     // in-lists from the deduplicated out-arcs: row of arc i is the source,
     // found by walking the offsets (build an explicit source array once)
-    HostVec<int32_t> row_of((size_t)std::max<int64_t>(total, 1));
+    HostVec<int32_t>& row_of = st.row_of;
+    row_of.resize((size_t)std::max<int64_t>(total, 1));
     parallel_for(n, n_threads(total), [&](int, int64_t lo, int64_t hi) {
         for (int64_t v = lo; v < hi; v++)
             for (int32_t i = G.out_off[v]; i < G.out_off[v + 1]; i++) row_of[i] = (int32_t)v;
     });
     build_side(n, total,
                [&](int64_t i) { return ((uint64_t)(uint32_t)G.out_adj[i] << 32) | (uint32_t)row_of[i]; }, G.in_off,
-               G.in_adj);
+               G.in_adj, st);
     return XM_OK;
 }
 
