@@ -158,18 +158,39 @@ __device__ __forceinline__ ListRef op_list(const GraphDev& g, int dir, int32_t v
     return r;
 }
 
-// Is x in the list whose hash table is tab[0..T)? Each bucket is one
-// 32-byte sector read as two 16-byte vectors; a bucket with an empty slot
-// ends the search (tables are at most half full).
+// One hash bucket (8 slots, one 32-byte sector) in a single 256-bit
+// read-only load. Buckets are 32-byte aligned: every table holds a power of
+// two >= 64 slots and starts at a multiple of 64 slots of a 256-byte aligned
+// allocation. One load per lane halves the L1 wavefronts of the two 16-byte
+// loads it replaces (the probe loops were L1-throughput bound).
+struct Bucket {
+    int32_t v[HASH_BUCKET];
+};
+__device__ __forceinline__ Bucket load_bucket(const int32_t* p) {
+    Bucket b;
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(b.v[0]), "=r"(b.v[1]), "=r"(b.v[2]), "=r"(b.v[3]), "=r"(b.v[4]), "=r"(b.v[5]), "=r"(b.v[6]),
+          "=r"(b.v[7])
+        : "l"(p));
+    return b;
+}
+__device__ __forceinline__ bool bucket_has(const Bucket& q, int32_t x) {
+    return q.v[0] == x || q.v[1] == x || q.v[2] == x || q.v[3] == x || q.v[4] == x || q.v[5] == x ||
+           q.v[6] == x || q.v[7] == x;
+}
+__device__ __forceinline__ bool bucket_open(const Bucket& q) {  // an empty slot (-1)
+    return (q.v[0] | q.v[1] | q.v[2] | q.v[3] | q.v[4] | q.v[5] | q.v[6] | q.v[7]) < 0;
+}
+
+// Is x in the list whose hash table is tab[0..T)? A bucket with an empty
+// slot ends the search (tables are at most half full).
 __device__ __forceinline__ bool hash_has(const int32_t* __restrict__ tab, uint32_t T, int32_t x) {
     const uint32_t nb = T / HASH_BUCKET;
     uint32_t b = hash_bucket(x, nb);
     for (uint32_t step = 0; step < nb; step++) {
-        const int4* q = reinterpret_cast<const int4*>(tab + (size_t)b * HASH_BUCKET);
-        const int4 a = __ldg(q), c = __ldg(q + 1);
-        if (a.x == x || a.y == x || a.z == x || a.w == x || c.x == x || c.y == x || c.z == x || c.w == x)
-            return true;
-        if ((a.x | a.y | a.z | a.w | c.x | c.y | c.z | c.w) < 0) return false;  // an empty slot (-1)
+        const Bucket q = load_bucket(tab + (size_t)b * HASH_BUCKET);
+        if (bucket_has(q, x)) return true;
+        if (bucket_open(q)) return false;
         b = (b + 1) & (nb - 1);
     }
     return false;
@@ -180,10 +201,9 @@ __device__ __forceinline__ bool hash_has(const int32_t* __restrict__ tab, uint32
 // settles the answer (x found, or an empty slot seen).
 __device__ __forceinline__ bool hash_first(const int32_t* __restrict__ tab, uint32_t T, int32_t x, bool& found) {
     const uint32_t b = hash_bucket(x, T / HASH_BUCKET);
-    const int4* q = reinterpret_cast<const int4*>(tab + (size_t)b * HASH_BUCKET);
-    const int4 a = __ldg(q), c = __ldg(q + 1);
-    found = a.x == x || a.y == x || a.z == x || a.w == x || c.x == x || c.y == x || c.z == x || c.w == x;
-    return found || (a.x | a.y | a.z | a.w | c.x | c.y | c.z | c.w) < 0;
+    const Bucket q = load_bucket(tab + (size_t)b * HASH_BUCKET);
+    found = bucket_has(q, x);
+    return found || bucket_open(q);
 }
 
 // Order bounds of a level: candidates x must satisfy lo < x < hi.
