@@ -162,13 +162,14 @@ __device__ __forceinline__ ListRef op_list(const GraphDev& g, int dir, int32_t v
 // read-only load. Buckets are 32-byte aligned: every table holds a power of
 // two >= 64 slots and starts at a multiple of 64 slots of a 256-byte aligned
 // allocation. One load per lane halves the L1 wavefronts of the two 16-byte
-// loads it replaces (the probe loops were L1-throughput bound).
+// loads it replaces (the probe loops were L1-throughput bound); random
+// buckets are not kept in L1, which stays for the lists and offsets.
 struct Bucket {
     int32_t v[HASH_BUCKET];
 };
 __device__ __forceinline__ Bucket load_bucket(const int32_t* p) {
     Bucket b;
-    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm("ld.global.nc.L1::no_allocate.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(b.v[0]), "=r"(b.v[1]), "=r"(b.v[2]), "=r"(b.v[3]), "=r"(b.v[4]), "=r"(b.v[5]), "=r"(b.v[6]),
           "=r"(b.v[7])
         : "l"(p));
