@@ -99,6 +99,9 @@ int xm_version(void);
  * offsets) on the host and copies it to device memory owned by the handle,
  * together with the handle's scratch buffers (about 12 bytes per node and
  * 12 bytes per arc) and a hash index of the lists (up to 16 bytes per arc).
+ * The host arrays of the build are kept for the next load (process-wide;
+ * about 32 bytes per input arc and 28 bytes per node of the largest graph
+ * loaded so far), so loads from several threads take turns.
  * Errors: XM_EINVAL for n/m out of range or an id outside [0, n), or more
  * than 2^31-1 arcs after deduplication; XM_ENOMEM; XM_ECUDA.
  */
