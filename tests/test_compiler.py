@@ -281,6 +281,10 @@ SPLIT_PATTERNS = {
     "bowtie": (5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2)]),
     "four_parts": (6, [(0, 1), (1, 0), (0, 2), (2, 3), (3, 0), (4, 0), (0, 5)]),
     "recip_path": (5, [(0, 1), (1, 0), (1, 2), (2, 3), (3, 2), (3, 4)]),
+    # eight vertices: dozens of quotient classes, split again recursively
+    "path8": (8, [(i, i + 1) for i in range(7)]),
+    "spider8": (8, [(1, 0), (2, 1), (3, 0), (4, 3), (0, 5), (5, 6), (7, 0)]),
+    "double_star8": (8, [(0, 1), (0, 2), (0, 3), (0, 4), (4, 5), (4, 6), (4, 7)]),
 }
 
 

@@ -472,6 +472,23 @@ SPLIT_PATTERNS = {
 }
 
 
+@pytest.mark.parametrize("name", ["path8", "spider8", "double_star8"])
+def test_split_counts_eight_vertices(xm, name):
+    """Eight-vertex patterns whose splits have dozens of quotient classes,
+    themselves split again, on a sparse ER graph the oracle walks quickly."""
+    pat = {"path8": (8, [(i, i + 1) for i in range(7)]),
+           "spider8": (8, [(1, 0), (2, 1), (3, 0), (4, 3), (0, 5), (5, 6), (7, 0)]),
+           "double_star8": (8, [(0, 1), (0, 2), (0, 3), (0, 4), (4, 5), (4, 6), (4, 7)])}[name]
+    n, src, dst = synth.er_graph(300, 900, seed=9)
+    g, og = graph_pair(xm, n, src, dst)
+    assert xm.Plan(pat).split()["cut"] >= 0
+    want = og.count_matches(pat)
+    assert want > 0
+    for flags in (xm.XM_REDUCE, xm.XM_NO_SPLIT, xm.XM_NO_PRODUCT | xm.XM_NO_REDUCE):
+        assert xm.xm_count(g, xm.Plan(pat, flags)) == want, flags
+    assert xm.xm_count(g, xm.Plan(pat, xm.XM_EMBEDDINGS)) == og.count_embeddings(pat)
+
+
 @pytest.mark.parametrize("name", sorted(SPLIT_PATTERNS))
 def test_split_counts(xm, tiny, rmat_tiny, name):
     """xm_count through the cut-vertex decomposition (per-node part counts,
