@@ -913,6 +913,121 @@ __global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     }
 }
 
+// Three-vertex plans, count mode: the last level of the partial match
+// (m0, m1) over the driver piece [pos0, pos0 + per) of its cut range, with
+// the lists in registers instead of a level state in shared memory (the
+// general path's per-unit set-up dominated these kernels' shared-memory and
+// local-memory traffic). Chooses the driver and cut exactly as setup_level
+// and level2_cut do, so the pieces match the work units. Returns false
+// (nothing counted) when the level needs the general path: difference
+// lists, more than two probe lists, or a probe without a hash table.
+// Survivors are counted per lane into acc.
+__device__ __forceinline__ bool leaf3_direct(const XmPlanDev& P, const GraphDev& g, int32_t m0, int32_t m1,
+                                             const int32_t* set, int set_len, int pos0, int per, int lane,
+                                             unsigned long long& acc) {
+    const XmLevel& L = P.lv[2];
+    if (L.ndiff) return false;
+    ListRef mine{nullptr, 0, 0, nullptr, 0};
+    if (lane < L.nops) mine = op_list(g, L.op_dir[lane], L.op_level[lane] ? m1 : m0);
+    bool use_reuse = L.reuse == 1;
+    if (use_reuse && __popc(L.reuse_ops) == 1) {
+        const int len_i = __shfl_sync(FULL, mine.len, __ffs(L.reuse_ops) - 1);
+        if (len_i == set_len) use_reuse = false;
+    }
+    // lists in setup_level's order: the reused set, then the remaining
+    // operands; the driver is the first shortest
+    int dsrc = -2, dlen = INT_MAX, nlists = 0;
+    bool empty = false;
+    if (use_reuse) {
+        dsrc = -1;
+        dlen = set_len;
+        nlists = 1;
+        empty = set_len == 0;
+    }
+    for (int i = 0; i < L.nops; i++) {
+        if (use_reuse && ((L.reuse_ops >> i) & 1u)) continue;
+        const int len = __shfl_sync(FULL, mine.len, i);
+        nlists++;
+        if (len == 0) empty = true;
+        if (len < dlen) {
+            dlen = len;
+            dsrc = i;
+        }
+    }
+    if (nlists > 3 || (use_reuse && dsrc != -1)) return false;  // > 2 probes, or the set as a probe
+    // probes: the operands other than the driver, each with a hash table
+    const int32_t* tab[2] = {nullptr, nullptr};
+    uint32_t T[2] = {0, 0};
+    int np = 0;
+    bool hashed = true;
+    for (int i = 0; i < L.nops; i++) {
+        if (i == dsrc || (use_reuse && ((L.reuse_ops >> i) & 1u))) continue;
+        const uint32_t Ti = __shfl_sync(FULL, mine.T, i);
+        const int32_t* ti =
+            reinterpret_cast<const int32_t*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.tab), i));
+        if (!Ti) hashed = false;
+        if (np < 2) {
+            tab[np] = ti;
+            T[np] = Ti;
+        }
+        np++;
+    }
+    if (!hashed) return false;
+    const int32_t* dp =
+        dsrc == -1 ? set
+                   : reinterpret_cast<const int32_t*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.p), dsrc));
+    if (empty) return true;
+    const int32_t m[2] = {m0, m1};
+    int32_t lo, hi;
+    level_bounds(L, m, lo, hi);
+    int c0 = 0, c1 = dlen;
+    if (lo >= 0) c0 = lbound(dp, 0, c1, lo + 1, false);
+    if (hi != INT_MAX) c1 = lbound(dp, c0, c1, hi, false);
+    const int pos = min(c1, c0 + pos0);
+    const int end = min(c1, pos + per);
+    if (pos >= end) return true;
+    // matched nodes that may lie in the candidates (-1: none)
+    const int32_t y0 = (L.neq_mask & 1u) ? m0 : -1;
+    const int32_t y1 = (L.neq_mask & 2u) ? m1 : -1;
+    if (np == 0) {
+        if (lane == 0) {
+            long long c = end - pos;
+            for (int32_t y : {y0, y1}) {
+                if (y < 0) continue;
+                const int q = lbound(dp, pos, end, y, false);
+                if (q < end && __ldg(dp + q) == y) c--;
+            }
+            acc += c;
+        }
+        return true;
+    }
+    unsigned cnt = 0;
+    for (int base = pos; base < end; base += 128) {
+        int32_t x[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = base + 32 * u + lane;
+            ok[u] = i < end;
+            x[u] = ok[u] ? __ldg(dp + i) : 0;
+        }
+        for (int p = 0; p < np; p++) {
+            const int32_t* tb = tab[p];
+            const uint32_t Tp = T[p];
+            bool f[4], dn[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) dn[u] = ok[u] ? hash_first(tb, Tp, x[u], f[u]) : (f[u] = false, true);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (ok[u]) ok[u] = dn[u] ? f[u] : hash_has(tb, Tp, x[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) cnt += (ok[u] && x[u] != y0 && x[u] != y1) ? 1u : 0u;
+    }
+    acc += cnt;
+    return true;
+}
+
 // Three-vertex plans whose last level needs no intersection per partial
 // match (leaf_kind, chosen on the host by leaf_closed_form_kind):
 //   1: the last level's candidates are the first level's set itself (reuse
@@ -1085,6 +1200,10 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
             const int e = owner;
             const int root = __ldg(ra.l1root + e);
             const int s0 = set_start(ra, root), s1 = set_start(ra, root + 1);
+            if (MODE == MODE_COUNT && ke == 3 &&
+                leaf3_direct(P, g, root_node(ra, root), __ldg(ra.l1set + e), ra.l1set + s0, s1 - s0, chunk * per2,
+                             per2, lane, acc))
+                continue;
             if (lane == 0) {
                 ws.m[0] = root_node(ra, root);
                 ws.m[1] = __ldg(ra.l1set + e);
