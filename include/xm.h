@@ -340,8 +340,13 @@ int xm_plan_tune(xm_graph g, xm_plan p, const xm_tuning *cand, int32_t ncand, in
 /*
  * xm_count -- number of matches of plan p in graph g (Alg. 2 plan
  * execution with count-only result generation, Sec. 5.3).
- * Writes the 128-bit count as (*lo, *hi). Synchronises `stream`.
- * Errors: XM_EINVAL (NULL handle/output), XM_ECUDA.
+ * Uses the plan's leaf product (xm_plan_product) and, for the whole graph,
+ * its cut-vertex decomposition (xm_plan_split: several launches and host
+ * steps, per-node counters of 16 B x n per part allocated with the graph
+ * on first use). Writes the 128-bit count as (*lo, *hi). Synchronises
+ * `stream`.
+ * Errors: XM_EINVAL (NULL handle/output), XM_ETIMEOUT (tuning budget spent
+ * in one of the launches), XM_ENOMEM, XM_ECUDA.
  */
 int xm_count(xm_graph g, xm_plan p, uint64_t *lo, uint64_t *hi, void *stream);
 
@@ -350,6 +355,7 @@ int xm_count(xm_graph g, xm_plan p, uint64_t *lo, uint64_t *hi, void *stream);
  * vertex (xm_plan_info's `start`) is mapped to a node in [root_lo, root_hi)
  * (Alg. 2 parallelises over the start vertex's candidates). Counts over a
  * partition of [0, n) add up to xm_count. Ranges are clipped to [0, n).
+ * Uses the leaf product but never the cut-vertex decomposition.
  */
 int xm_count_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t *lo, uint64_t *hi,
                    void *stream);
