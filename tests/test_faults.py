@@ -27,6 +27,28 @@ def test_null_arguments_return_einval():
     assert L.xm_strerror(99) == b"XM_UNKNOWN"
 
 
+def test_product_and_split_queries_reject_bad_arguments():
+    L = xm.lib()
+    info = xm.xm_level_info()
+    i32 = ctypes.c_int32
+    assert L.xm_plan_product(None, None, None, None, None) == xm.XM_EINVAL
+    assert L.xm_plan_split(None, None, None, None, None) == xm.XM_EINVAL
+    star = xm.Plan((4, [(0, 1), (0, 2), (0, 3)]))           # choose product, no split
+    assert L.xm_plan_product_set(star._h, 1, ctypes.byref(info)) == xm.XM_EINVAL
+    assert L.xm_plan_product_set(star._h, -1, ctypes.byref(info)) == xm.XM_EINVAL
+    assert L.xm_plan_product_set(star._h, 0, ctypes.byref(info)) == xm.XM_OK
+    buf = (i32 * 56)()
+    assert L.xm_plan_split_part(star._h, 0, None, None, buf, buf, None, None) == xm.XM_EINVAL
+    assert L.xm_plan_split_quotient(star._h, 0, None, None, buf, buf, None) == xm.XM_EINVAL
+    chain = xm.Plan(synth.FFCHAIN5)
+    sp = chain.split()
+    assert L.xm_plan_split_part(chain._h, len(sp["parts"]), None, None, buf, buf, None, None) == xm.XM_EINVAL
+    assert L.xm_plan_split_quotient(chain._h, len(sp["quotients"]), None, None, buf, buf, None) == xm.XM_EINVAL
+    # unknown flag bits
+    ps, pd = (i32 * 1)(0), (i32 * 1)(1)
+    assert L.xm_compile_pattern(2, 1, ps, pd, 32, ctypes.byref(ctypes.c_void_p())) == xm.XM_EINVAL
+
+
 def test_bad_tuning_rejected():
     p = xm.Plan(synth.FFL)
     for bad in (dict(window=48), dict(unit=0, window=5000), dict(warps_per_block=17), dict(budget_ms=-1)):
