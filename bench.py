@@ -149,6 +149,15 @@ def profiled_traffic(workload_name):
     return None
 
 
+def start_node_sample(n, one_in):
+    """The start nodes a sampled workload counts from: a seeded uniform
+    sample of n // one_in nodes (the paper's runs from a percentage of the
+    start nodes, Sec. 6.4), sorted."""
+    rng = np.random.default_rng(24)
+    roots = np.sort(rng.choice(n, n // one_in, replace=False)).astype(np.int32)
+    return roots, f"start nodes: seeded uniform sample of 1/{one_in} ({len(roots)} nodes)"
+
+
 # ------------------------------------------------------- sharding (N > 1) --
 
 def shard_bounds(n, src, dst, world):
@@ -175,29 +184,46 @@ def allreduce_counts(counts, dist, device="cpu"):
 
 # ----------------------------------------------------------- oracle (CPU) --
 
-def oracle_sample(n, src, dst, pats, budget_s, seed=0):
-    """The CPU oracle as it stands, single-threaded, on seeded uniform start
-    nodes: embeddings rooted at pattern vertex 0, converted to matches
-    (divided by |Aut|). Runs start nodes until budget_s per pattern."""
+# a rooted oracle walk stops after this many candidates (some scale-24 start
+# nodes would take it hours); its time still counts
+ORACLE_ROOT_CAP = 20_000_000
+_OG_CACHE = {}
+
+
+def oracle_sample(n, src, dst, pats, budget_s, seed=0, roots=None):
+    """The CPU oracle as it stands, single-threaded, on start nodes in seeded
+    order (all nodes, or the given sample): embeddings rooted at pattern
+    vertex 0, converted to matches (divided by |Aut|). Runs start nodes until
+    budget_s per pattern. Returns (matches, seconds, start nodes, walks
+    stopped at the cap)."""
     import oracle
-    og = oracle.OracleGraph(n, src, dst)
+    key = (n, len(src))
+    if key not in _OG_CACHE:
+        _OG_CACHE.clear()
+        _OG_CACHE[key] = oracle.OracleGraph(n, src, dst)
+    og = _OG_CACHE[key]
     rng = np.random.default_rng(seed)
-    roots = rng.permutation(n)
+    order = rng.permutation(n) if roots is None else rng.permutation(np.asarray(roots))
     per = budget_s / len(pats)
     matches = 0.0
     spent = 0.0
     nroots = 0
+    gave_up = 0
     for pat in pats.values():
         aut = oracle.automorphisms(pat).shape[0]
         t0 = time.perf_counter()
         i = 0
-        while time.perf_counter() - t0 < per and i < n:
-            r = int(roots[i])
-            matches += og.count_embeddings(pat, 0, r, r + 1) / aut
+        while time.perf_counter() - t0 < per and i < len(order):
+            r = int(order[i])
+            c = og.count_embeddings_capped(pat, 0, r, r + 1, ORACLE_ROOT_CAP)
+            if c is None:
+                gave_up += 1
+            else:
+                matches += c / aut
             i += 1
         spent += time.perf_counter() - t0
         nroots += i
-    return matches, spent, nroots
+    return matches, spent, nroots, gave_up
 
 
 def _oracle_worker(job):
@@ -207,7 +233,7 @@ def _oracle_worker(job):
     n, src, dst, pats, _ = workload(name)
     if pattern_names:
         pats = {k: v for k, v in pats.items() if k in pattern_names}
-    return oracle_sample(n, src, dst, pats, budget_s=budget_s, seed=1000 + seed)
+    return oracle_sample(n, src, dst, pats, budget_s=budget_s, seed=1000 + seed)[:3]
 
 
 def oracle_all_cores(name, pattern_names, procs, budget_s):
@@ -227,16 +253,27 @@ def run_reference(args):
     if rank != 0:
         return 0
     n, src, dst, pats, desc = workload(args.workload)
+    if args.patterns:
+        pats = {k: v for k, v in pats.items() if k in args.patterns.split(",")}
+        desc += f" (subset: {','.join(pats)})"
+    roots = None
+    if args.workload in ("rmat22", "rmat24"):
+        roots, sample_desc = start_node_sample(n, args.root_sample)
+        desc += "; " + sample_desc
     vals = []
     last = None
     for step in range(args.warmup + args.steps):
-        matches, secs, nroots = oracle_sample(n, src, dst, pats, budget_s=args.ref_budget, seed=step)
+        matches, secs, nroots, gave_up = oracle_sample(n, src, dst, pats, budget_s=args.ref_budget, seed=step,
+                                                       roots=roots)
         if step >= args.warmup:
             vals.append(matches / secs)
-            last = (nroots, secs)
+            last = (nroots, secs, gave_up)
     v = statistics.median(vals)
-    sample = (f"{last[0]} seeded uniform start nodes over the {len(pats)} patterns (~{args.ref_budget:.0f} s of "
-              f"single-threaded oracle time per step); matches = rooted embeddings / |Aut|")
+    sample = ((f"{last[0]} start nodes of the same sample" if roots is not None else
+               f"{last[0]} seeded uniform start nodes") +
+              f" over the {len(pats)} patterns (~{args.ref_budget:.0f} s of single-threaded oracle time per step"
+              + (f"; {last[2]} walks over {ORACLE_ROOT_CAP:.0e} candidates stopped, time counted, matches not"
+                 if last[2] else "") + "); matches = rooted embeddings / |Aut|")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "matches/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * last[1], "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -474,6 +511,9 @@ def main():
     ap.add_argument("--root-sample", type=int, default=1024,
                     help="rmat24: count over a seeded uniform sample of 1/N of the start nodes")
     ap.add_argument("--budget-ms", type=int, default=0, help="device-time budget per count call (0: none)")
+    ap.add_argument("--merge-ratio", type=int, default=0,
+                    help="intersection strategy threshold of two-list last levels (0: library default, -1: "
+                         "never merge)")
     ap.add_argument("--no-tune", action="store_true", help="skip the per-pattern autotuner (warm-up phase)")
     ap.add_argument("--ablation", action="store_true",
                     help="also time every pattern with its unreduced plan (no candidate-set reuse)")
@@ -483,6 +523,8 @@ def main():
     ap.add_argument("--walk-budget-ms", type=int, default=20000, help="0: skip the walks")
     ap.add_argument("--enum-capacity", type=int, default=1 << 24,
                     help="rmat24: matches written by the untimed enumeration check")
+    ap.add_argument("--no-whole-ffchain", action="store_true",
+                    help="rmat24: skip the whole-graph feed-forward chain count through the split")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -509,19 +551,14 @@ def main():
         desc += f" (subset: {','.join(pats)})"
     g = xm.Graph(n, src, dst)
     plans = {name: xm.Plan(p) for name, p in pats.items()}
-    if args.budget_ms:
-        for p in plans.values():
-            p.set_tuning(budget_ms=args.budget_ms)
+    for p in plans.values():
+        p.set_tuning(budget_ms=args.budget_ms, merge_ratio=args.merge_ratio)
     r_lo, r_hi = shard_bounds(n, src, dst, world)[rank]
     roots = None
     if args.workload in ("rmat22", "rmat24"):
-        # a seeded uniform sample of the start nodes (the paper's percentage-
-        # of-start-nodes runs); a full scale-24 count of these patterns is
-        # far beyond a one-minute step
-        rng = np.random.default_rng(24)
-        roots = np.sort(rng.choice(n, n // args.root_sample, replace=False)).astype(np.int32)
+        roots, sample_desc = start_node_sample(n, args.root_sample)
         roots = roots[(roots >= r_lo) & (roots < r_hi)]
-        desc += f"; start nodes: seeded uniform sample of 1/{args.root_sample} ({len(roots)} nodes)"
+        desc += "; " + sample_desc
 
     def count_one(p):
         if roots is not None:
@@ -540,19 +577,20 @@ def main():
         return counts
 
     tuned = {}
-    if not args.no_tune:
-        # project autotuner (untimed, part of warm-up): window, warps per
-        # block and unit size per pattern on this graph
-        cands = [(w, u, wpb, 0, args.budget_ms) for w in (256, 512) for wpb in (4, 8, 16) for u in (8, 32)]
+    if not args.no_tune and world == 1:
+        # project autotuner (untimed, part of warm-up): window, unit size,
+        # warps per block and the intersection strategy's length ratio, per
+        # pattern on this graph (on the start-node sample when there is one)
+        cands = [(w, u, wpb, 0, args.budget_ms, mr) for w in (256, 512) for wpb in (4, 8) for u in (8, 32)
+                 for mr in ((args.merge_ratio,) if args.merge_ratio else (-1, 8))]
         for name, p in plans.items():
-            if roots is None and world == 1:
-                best, _ = xm.xm_plan_tune(g, p, cands, reps=1)
-                tuned[name] = {k: best[k] for k in ("window", "unit", "warps_per_block")}
+            best, _ = xm.xm_plan_tune(g, p, cands, reps=1, roots=roots)
+            tuned[name] = {k: best[k] for k in ("window", "unit", "warps_per_block", "merge_ratio")}
     for _ in range(args.warmup):
         counts = step()
 
-    kernel_ms = []
-    per_pattern_ms = {name: [] for name in plans}
+    kernel_ms = {name: [] for name in plans}
+    prep_ms = {name: [] for name in plans}
     step_ms = []
     if world > 1:
         dist.barrier()
@@ -567,8 +605,8 @@ def main():
             for name, p in plans.items():
                 counts[name] = count_one(p)
                 prep, match = g.last_timing()
-                kernel_ms.append(match)
-                per_pattern_ms[name].append(prep + match)
+                kernel_ms[name].append(match)
+                prep_ms[name].append(prep)
             ev1.record(stream)
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
@@ -587,9 +625,14 @@ def main():
         dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (the matcher): algorithmic bytes from an
-    # instrumented, untimed run; duration from the CUDA events of the timed runs
-    alg_bytes = 0
+    # Roofline of the dominant kernel, the persistent matcher k_match (one
+    # launch per pattern per step): its algorithmic bytes (an instrumented,
+    # untimed run that takes the same code paths) over its own CUDA-event
+    # time in the timed steps. The first-level pass before it (k_l1 and the
+    # scans, prep_ms) gets its own line.
+    peak, peak_kind = measured_peaks()
+    per_pattern = {}
+    alg_total = touched_total = l1_total = 0
     extensions = 0
     if not args.no_stats:
         for name, p in plans.items():
@@ -598,24 +641,38 @@ def main():
             else:
                 c, st = xm.xm_count_stats(g, p, r_lo, r_hi)
             assert c == counts[name] or world > 1
-            alg_bytes += st["alg_bytes"]
+            kms = statistics.median(kernel_ms[name])
+            per_pattern[name] = {"matcher_ms": round(kms, 3), "prep_ms": round(statistics.median(prep_ms[name]), 3),
+                                 "alg_bytes": st["alg_bytes"], "touched_bytes": st["touched_bytes"],
+                                 "alg_gbs": round(st["alg_bytes"] / kms / 1e6, 1),
+                                 "frac": round(st["alg_bytes"] / kms / 1e6 / peak, 4),
+                                 "warp_exit_ms": [round(st[k] / 1e6, 2) for k in
+                                                  ("warp_exit_first_ns", "warp_exit_mean_ns", "warp_exit_last_ns")]}
+            alg_total += st["alg_bytes"]
+            touched_total += st["touched_bytes"]
+            l1_total += st["l1_bytes"]
             extensions += st["extensions"]
-    launches = len(plans) * args.steps
-    avg_kernel_s = sum(kernel_ms) / len(kernel_ms) / 1000.0
-    bytes_per_launch = alg_bytes / len(plans)
-    achieved = bytes_per_launch / avg_kernel_s / 1e9
-    peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic(args.workload)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+    kernel_s = sum(statistics.median(v) for v in kernel_ms.values()) / 1000.0   # per step
+    prep_s = sum(statistics.median(v) for v in prep_ms.values()) / 1000.0
+    launches = len(plans)
+    achieved = alg_total / kernel_s / 1e9 if alg_total else None
+    traffic = profiled_traffic(args.workload)   # ncu DRAM bytes per matcher launch, current kernel only
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
                 "traffic": traffic, "peak_source": peak_kind,
-                # against the nominal 7.7 TB/s, and DRAM bytes (ncu) per second
-                "frac_of_nominal": achieved / 7700.0,
-                "dram_gbs": None if traffic is None else traffic / avg_kernel_s / 1e9,
-                "dram_frac": None if traffic is None else traffic / avg_kernel_s / 1e9 / peak,
-                # partial matches extended per second of matcher time (instrumented run's count)
-                "extensions_per_s": extensions / (sum(kernel_ms) / args.steps / 1000.0) if extensions else None,
-                "kernel": "k_match (persistent matcher)", "kernel_share_of_step":
-                    sum(kernel_ms) / sum(step_ms)}
+                "alg_bytes_per_launch": alg_total / launches if alg_total else None,
+                "kernel_ms_per_launch": kernel_s * 1000.0 / launches,
+                "kernel": "k_match (persistent matcher)", "kernel_share_of_step": kernel_s * 1000.0 / ms,
+                # DRAM bytes (ncu) per second of matcher time: the HBM traffic the kernel really moves
+                "dram_gbs": None if traffic is None else traffic / (kernel_s / launches) / 1e9,
+                "dram_frac": None if traffic is None else traffic / (kernel_s / launches) / 1e9 / peak,
+                # bytes the chosen strategies would move with no cache, for comparison with DRAM traffic
+                "touched_bytes_per_launch": touched_total / launches if touched_total else None,
+                "frac_of_nominal": achieved / 7700.0 if achieved else None,
+                "extensions_per_s": extensions / kernel_s if extensions else None,
+                "per_pattern": per_pattern,
+                "first_level_pass": {"alg_bytes": l1_total, "ms": round(prep_s * 1000.0, 3),
+                                     "alg_gbs": round(l1_total / prep_s / 1e9, 1) if prep_s else None}}
 
     ablation = None
     if args.ablation:
@@ -730,12 +787,37 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(plans) * 128,
                "ms_per_step": statistics.median(e2e_ms)}
 
+    # the whole-graph count of the 5-vertex feed-forward chain through its
+    # cut-vertex decomposition (part counts per node, product sum, quotient
+    # counts: several launches and host steps), beside the sampled step
+    whole = None
+    if args.workload == "rmat24" and "ffchain5" in pats and not args.no_whole_ffchain:
+        pw = xm.Plan(synth.FFCHAIN5)
+        wms = []
+        for _ in range(3):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            cw = xm.xm_count(g, pw)
+            ev1.record(stream)
+            ev1.synchronize()
+            wms.append(ev0.elapsed_time(ev1))
+        sp = pw.split()
+        whole = {"pattern": "ffchain5", "count": int(cw), "ms": round(min(wms), 2),
+                 "matches_per_s": cw / (min(wms) / 1000.0),
+                 "how": f"cut vertex {sp['cut']}: {len(sp['parts'])} rooted part counts per node, "
+                        f"{len(sp['quotients'])} quotient patterns (not in the timed step)"}
+
     cpu = None
     if not args.no_cpu_baseline:
-        m_, s_, nr = oracle_sample(n, src, dst, pats, budget_s=args.cpu_budget)
+        m_, s_, nr, gave_up = oracle_sample(n, src, dst, pats, budget_s=args.cpu_budget, roots=roots)
         cpu = {"value": m_ / s_, "unit": "matches/s", "cores": 1, "kind": "oracle",
-               "sample": f"{nr} seeded uniform start nodes over the {len(pats)} patterns, "
-                         f"{s_:.1f} s single-threaded; matches = rooted embeddings / |Aut|"}
+               "sample": (f"{nr} start nodes of the same sample" if roots is not None else
+                          f"{nr} seeded uniform start nodes") +
+                         f" over the {len(pats)} patterns, {s_:.1f} s single-threaded"
+                         + (f" ({gave_up} walks over {ORACLE_ROOT_CAP:.0e} candidates stopped, their time "
+                            f"counted, their matches not)" if gave_up else "")
+                         + "; matches = rooted embeddings / |Aut|"}
         if args.cpu_procs:
             procs = min(os.cpu_count() or 1, 64) if args.cpu_procs < 0 else args.cpu_procs
             rate, nr_all = oracle_all_cores(args.workload, list(pats), procs, args.cpu_budget)
@@ -751,11 +833,12 @@ def main():
                        "matches_per_step": total_matches, "l2": "flushed (512 MB write) between timed steps",
                        "parallelism": f"start-node shards x{world}" if world > 1 else "1 GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": LAUNCHES_PER_CALL * launches, "clocks": clocks,
-            "counts": {k: int(v) for k, v in counts.items()}, "enumeration": enum, "ablation": ablation,
-            "leaf_products": products,
+            "gpu_launches": LAUNCHES_PER_CALL * launches * args.steps, "clocks": clocks,
+            "counts": {k: int(v) for k, v in counts.items()}, "whole_graph": whole, "enumeration": enum,
+            "ablation": ablation, "leaf_products": products,
             "autotuned": tuned,
-            "device_ms_per_pattern": {k: round(statistics.median(v), 3) for k, v in per_pattern_ms.items()}}
+            "device_ms_per_pattern": {k: round(statistics.median(kernel_ms[k]) + statistics.median(prep_ms[k]), 3)
+                                      for k in plans}}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

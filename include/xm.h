@@ -78,6 +78,21 @@ const char *xm_last_error(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int xm_version(void);
 
+/*
+ * xm_fault_inject -- host-side fault injection, for tests of the error
+ * paths (no GPU fault is ever involved). spec: "alloc:N" makes the N-th
+ * device allocation of the library from now on fail as if the device were
+ * out of memory (the call reports XM_ENOMEM and releases what it had
+ * allocated); "compile:N" makes the N-th xm_compile_pattern from now on fail
+ * with XM_ENOMEM; several items comma-separated; "none" clears both. The
+ * environment variable XM_FAULT, read when the library loads, takes the same
+ * spec. Errors: XM_EINVAL for a malformed spec (nothing changes).
+ */
+int xm_fault_inject(const char *spec);
+
+/* Device memory currently held by the library (all handles), in bytes. */
+uint64_t xm_device_bytes_live(void);
+
 /* ------------------------------------------------------------- graphs */
 
 /*
@@ -304,13 +319,21 @@ void xm_plan_free(xm_plan p);
  *                    ids (multiple of 32, 64..4096);
  *   unit             positions of the first level's candidate list handed
  *                    out as one work unit (1..65536);
- *   warps_per_block  1..32;
+ *   warps_per_block  1..16;
  *   blocks_per_sm    resident blocks per SM to launch (persistent grid);
  *   budget_ms        work budget: when the matcher has run this long (GPU
  *                    global timer) every warp stops at its next check and
  *                    the call returns XM_ETIMEOUT with no count (0 = none).
  *                    The kernel always finishes and the context stays
- *                    usable.
+ *                    usable;
+ *   merge_ratio      intersection strategy of counted last levels with two
+ *                    lists (Alg. 2's A^{e.dest} cap Pi A^e): the longer list,
+ *                    cut to the shorter one's id range, is merged with it
+ *                    (both streamed in coalesced 16-byte loads) when it is at
+ *                    most merge_ratio times as long, and otherwise probed
+ *                    once per id of the shorter list (hash table, or binary
+ *                    search for lists under 32 ids). 1..1024; 0 = default
+ *                    (8); -1 = never merge. Counts never depend on it.
  */
 typedef struct {
     int32_t window;
@@ -318,6 +341,7 @@ typedef struct {
     int32_t warps_per_block;
     int32_t blocks_per_sm;
     int32_t budget_ms;  /* device-time budget of one call's matcher kernel, 0 = none */
+    int32_t merge_ratio;
 } xm_tuning;
 
 /* Sets the tuning used by later calls with this plan (copied). */
@@ -334,6 +358,14 @@ int xm_plan_get_tuning(xm_plan p, xm_tuning *t);
  */
 int xm_plan_tune(xm_graph g, xm_plan p, const xm_tuning *cand, int32_t ncand, int32_t reps, xm_tuning *best,
                  float *best_ms, void *stream);
+
+/*
+ * xm_plan_tune_roots -- xm_plan_tune on the counts of a start-node list
+ * (xm_count_roots; roots: host array of nroots node ids, as there), for
+ * workloads that count a sample of the start nodes.
+ */
+int xm_plan_tune_roots(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroots, const xm_tuning *cand,
+                       int32_t ncand, int32_t reps, xm_tuning *best, float *best_ms, void *stream);
 
 /* ------------------------------------------------------------ matching */
 
@@ -361,15 +393,33 @@ int xm_count_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint
                    void *stream);
 
 /*
- * Work and traffic counters of one instrumented run (xm_count_stats).
- *   alg_bytes     algorithmic bytes: per list operand 8 B of offsets plus
- *                 the cheaper of scanning the list or probing it once per
- *                 driver element (4 B x min(|L|, |C| x ceil(log2(|L|+1)))),
- *                 plus 8 B per degree check, 16 B per start-node check;
+ * Work and traffic counters of one instrumented run (xm_count_stats). The
+ * instrumented kernels take exactly the code paths of the counting kernels
+ * (same driver ranges, leaf shortcuts, merge-or-probe choices), so the
+ * bytes describe the timed work.
+ *   alg_bytes     algorithmic bytes of the persistent matcher (the kernel
+ *                 xm_graph_last_timing reports as match_ms): per list operand
+ *                 8 B of offsets; 4 B per driver id scanned; for every other
+ *                 list the cheaper of scanning it or probing it once per
+ *                 driver id, 4 B x min(|L|, |C| x ceil(log2(|L|+1))) with
+ *                 |L| cut to the driver range's ids where the kernel computes
+ *                 that cut (two-list last levels); 4 B x ceil(log2(L+1)) per
+ *                 bound search in a list of L ids; 8 B per degree check;
  *   extensions    partial matches created (descents into a level);
  *   set_ops       candidate sets computed (level set-ups);
  *   units         work units executed;
- *   leaf_elems    driver elements examined at the last level.
+ *   leaf_elems    driver elements examined at the last level;
+ *   l1_bytes      algorithmic bytes of the first-level pass (prep_ms): 16 B
+ *                 per start node checked, the first level's lists as above,
+ *                 8 B per first-level candidate written with its owner;
+ *   touched_bytes bytes the matcher's chosen strategies move at 32-byte-sector
+ *                 granularity if nothing were cached (a merge reads both
+ *                 ranges, a hash probe one sector, a binary search one sector
+ *                 per step above the last sector, offsets one sector);
+ *   warp_exit_first_ns / _mean_ns / _last_ns
+ *                 load balance of the instrumented matcher's persistent grid:
+ *                 when its warps ran out of work (earliest, mean, latest), in
+ *                 ns of the GPU global timer after the first warp started.
  */
 typedef struct {
     uint64_t alg_bytes;
@@ -377,7 +427,11 @@ typedef struct {
     uint64_t set_ops;
     uint64_t units;
     uint64_t leaf_elems;
-    uint64_t reserved[3];
+    uint64_t l1_bytes;
+    uint64_t touched_bytes;
+    uint64_t warp_exit_first_ns;
+    uint64_t warp_exit_mean_ns;
+    uint64_t warp_exit_last_ns;
 } xm_stats;
 
 /*
@@ -416,6 +470,21 @@ int xm_count_roots(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroots, 
                    void *stream);
 int xm_enumerate_roots(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroots, int32_t *dev_out,
                        uint64_t capacity, uint64_t *total, uint64_t *written, void *stream);
+/*
+ * xm_count_roots_each -- per-start-node counts: counts[2i], counts[2i+1]
+ * (host, caller-owned, 2 * nroots uint64) receive the 128-bit count (lo,
+ * hi) of the matches whose start vertex is mapped to roots[i] (embeddings
+ * with XM_EMBEDDINGS), in the caller's order; a node listed twice gets its
+ * count twice. One launch for all nodes: the matcher adds each work unit's
+ * count to a 128-bit device counter of its start node (Alg. 2 runs the
+ * start nodes as independent tasks, so the per-node counts add up to
+ * xm_count_roots). Uses the plan's leaf product, never the cut-vertex
+ * decomposition. Device counters: 16 B per distinct root, allocated with the
+ * graph on first use. Errors as xm_count_roots, XM_ENOMEM.
+ */
+int xm_count_roots_each(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroots, uint64_t *counts,
+                        void *stream);
+
 /* xm_count_roots with the xm_count_stats counters. */
 int xm_count_roots_stats(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroots, uint64_t *lo, uint64_t *hi,
                          xm_stats *stats, void *stream);
@@ -566,8 +635,10 @@ void xm_server_free(xm_server s);
  *
  * Limits and errors: XM_EINVAL when the scratch the graph needs (about
  * 4 bytes x (3n + 3.001m) plus small control data) exceeds
- * XM_NOALLOC_SCRATCH_BYTES -- use xm_count then --, or for NULL/invalid
- * sizes; XM_ECUDA when a CUDA call fails.
+ * XM_NOALLOC_SCRATCH_BYTES -- use xm_count then --, for NULL/invalid
+ * sizes, or when out_off[n] or in_off[n] differs from m (the call reads
+ * those two entries back before launching anything); XM_ECUDA when a CUDA
+ * call fails.
  * Set-up: the first call on each device looks up the scratch array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before capturing any stream into a CUDA graph.

@@ -64,6 +64,10 @@ def _L():
         lib.og_count_embeddings.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i32p, i32p,
                                             ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, u64ref, u64ref]
         lib.og_count_embeddings.restype = ctypes.c_int
+        lib.og_count_embeddings_capped.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i32p, i32p,
+                                                   ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
+                                                   ctypes.c_uint64, u64ref, u64ref]
+        lib.og_count_embeddings_capped.restype = ctypes.c_int
         lib.og_count_matches.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int,
                                          u64ref, u64ref]
         lib.og_count_matches.restype = ctypes.c_int
@@ -72,6 +76,12 @@ def _L():
         lib.og_enumerate.restype = ctypes.c_int64
         lib.og_canonicalize.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int64, i32p, i32p]
         lib.og_canonicalize.restype = None
+        lib.og_enumerate_embeddings.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_int64]
+        lib.og_enumerate_embeddings.restype = ctypes.c_int64
+        lib.og_triangle_sums.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, u64ref, u64ref]
+        lib.og_triangle_sums.restype = None
         _lib = lib
     return _lib
 
@@ -131,6 +141,18 @@ class OracleGraph:
             raise ValueError("bad pattern")
         return (hi.value << 64) | lo.value
 
+    def count_embeddings_capped(self, pattern, root: int, r_lo: int, r_hi: int, max_steps: int,
+                                induced: bool = False):
+        """count_embeddings, or None when the walk would examine more than
+        max_steps candidates."""
+        k, e, ps, pd = _pattern_arrays(pattern)
+        lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
+        rc = _L().og_count_embeddings_capped(self._h, k, e, ps, pd, root, r_lo, r_hi, int(induced), max_steps,
+                                             ctypes.byref(lo), ctypes.byref(hi))
+        if rc < 0:
+            raise ValueError("bad pattern")
+        return None if rc == 1 else (hi.value << 64) | lo.value
+
     def count_matches(self, pattern, induced: bool = False) -> int:
         """Distinct matched subgraphs (orbit-smallest embeddings)."""
         k, e, ps, pd = _pattern_arrays(pattern)
@@ -149,6 +171,27 @@ class OracleGraph:
         total = int(_L().og_enumerate(self._h, k, e, ps, pd, int(induced), buf.ctypes.data, capacity))
         rows = buf[: min(total, capacity) * k].reshape(-1, k)
         return sort_rows(rows)
+
+
+    def enumerate_embeddings(self, pattern, root: int = 0, r_lo: int = 0, r_hi: int | None = None,
+                             induced: bool = False) -> np.ndarray:
+        """Every embedding m with m(root) in [r_lo, r_hi), as an (N, k) int32
+        array in pattern-vertex order, rows sorted lexicographically."""
+        k, e, ps, pd = _pattern_arrays(pattern)
+        r_hi = self.n if r_hi is None else r_hi
+        total = int(_L().og_enumerate_embeddings(self._h, k, e, ps, pd, root, r_lo, r_hi, int(induced), None, 0))
+        if total < 0:
+            raise ValueError("bad pattern")
+        buf = np.empty(max(total, 1) * k, np.int32)
+        _L().og_enumerate_embeddings(self._h, k, e, ps, pd, root, r_lo, r_hi, int(induced), buf.ctypes.data, total)
+        return sort_rows(buf[: total * k].reshape(-1, k))
+
+    def triangle_sums(self, u_lo: int = 0, u_hi: int | None = None):
+        """(feed-forward triangles, closed 3-walks) over the arcs whose source
+        is in [u_lo, u_hi): over all nodes sum(A o A^2) and tr(A^3)."""
+        f, c = ctypes.c_uint64(), ctypes.c_uint64()
+        _L().og_triangle_sums(self._h, u_lo, self.n if u_hi is None else u_hi, ctypes.byref(f), ctypes.byref(c))
+        return f.value, c.value
 
 
 def canonicalize(pattern, tuples: np.ndarray) -> np.ndarray:

@@ -183,6 +183,9 @@ typedef struct {
     unsigned __int128 count;
     int32_t *out;
     int64_t capacity;
+    /* work cap: candidates examined so far, the cap (0: none), set when hit */
+    uint64_t steps, max_steps;
+    int gave_up;
 } og_search;
 
 /* breadth-first order over the undirected pattern from `root`, neighbours by
@@ -258,11 +261,18 @@ static void record(og_search *s) {
     s->count++;
 }
 
+/* One more candidate examined; 1 when the work cap is exceeded. */
+static int over_cap(og_search *s) {
+    s->steps++;
+    if (s->max_steps && s->steps > s->max_steps) s->gave_up = 1;
+    return s->gave_up;
+}
+
 static void extend(og_search *s, int d) {
     if (d == s->k) { record(s); return; }
     int v = s->order[d];
     if (d == 0) {
-        for (int32_t x = s->r_lo; x < s->r_hi; x++) {
+        for (int32_t x = s->r_lo; x < s->r_hi && !s->gave_up; x++) {
             s->m[v] = x;
             extend(s, 1);
         }
@@ -270,7 +280,7 @@ static void extend(og_search *s, int d) {
     }
     int u = s->parent[v];
     if (u < 0) { /* no matched neighbour: every node is a candidate */
-        for (int32_t x = 0; x < s->g->n; x++)
+        for (int32_t x = 0; x < s->g->n && !over_cap(s); x++)
             if (consistent(s, d, v, x)) { s->m[v] = x; extend(s, d + 1); }
         return;
     }
@@ -278,7 +288,7 @@ static void extend(og_search *s, int d) {
     int32_t mu = s->m[u];
     const int32_t *list = s->parent_out[v] ? g->out_adj + g->out_off[mu] : g->in_adj + g->in_off[mu];
     int64_t len = s->parent_out[v] ? g->out_off[mu + 1] - g->out_off[mu] : g->in_off[mu + 1] - g->in_off[mu];
-    for (int64_t i = 0; i < len; i++) {
+    for (int64_t i = 0; i < len && !over_cap(s); i++) {
         int32_t x = list[i];
         if (consistent(s, d, v, x)) { s->m[v] = x; extend(s, d + 1); }
     }
@@ -303,6 +313,22 @@ int og_count_embeddings(const og_graph *g, int k, int e, const int32_t *ps, cons
     og_search s;
     if (setup(&s, g, k, e, ps, pd, root, r_lo, r_hi, induced)) return -1;
     extend(&s, 0);
+    *lo = (uint64_t)s.count;
+    *hi = (uint64_t)(s.count >> 64);
+    return 0;
+}
+
+/* og_count_embeddings that gives up after examining max_steps candidates
+ * (summed over all levels of the walk): returns 1 (no count) when it gave
+ * up, 0 with the exact count otherwise. */
+int og_count_embeddings_capped(const og_graph *g, int k, int e, const int32_t *ps, const int32_t *pd, int root,
+                               int32_t r_lo, int32_t r_hi, int induced, uint64_t max_steps, uint64_t *lo,
+                               uint64_t *hi) {
+    og_search s;
+    if (setup(&s, g, k, e, ps, pd, root, r_lo, r_hi, induced)) return -1;
+    s.max_steps = max_steps;
+    extend(&s, 0);
+    if (s.gave_up) return 1;
     *lo = (uint64_t)s.count;
     *hi = (uint64_t)(s.count >> 64);
     return 0;
@@ -342,6 +368,60 @@ int64_t og_enumerate(const og_graph *g, int k, int e, const int32_t *ps, const i
     extend(&s, 0);
     free(aut);
     return (int64_t)s.count;
+}
+
+/* Writes up to `capacity` embeddings whose root pattern vertex maps into
+ * [r_lo, r_hi) (k node ids each, in pattern-vertex order) in search order;
+ * returns how many there are. Every embedding is written, not one per orbit. */
+int64_t og_enumerate_embeddings(const og_graph *g, int k, int e, const int32_t *ps, const int32_t *pd, int root,
+                                int32_t r_lo, int32_t r_hi, int induced, int32_t *out, int64_t capacity) {
+    og_search s;
+    if (setup(&s, g, k, e, ps, pd, root, r_lo, r_hi, induced)) return -1;
+    s.out = out;
+    s.capacity = capacity;
+    extend(&s, 0);
+    return (int64_t)s.count;
+}
+
+/* |a ∩ b| of two ascending lists: each id of the shorter looked up in the
+ * longer by binary search. */
+static uint64_t common_ids(const int32_t *a, int64_t na, const int32_t *b, int64_t nb) {
+    if (na > nb) { const int32_t *t = a; a = b; b = t; int64_t tn = na; na = nb; nb = tn; }
+    uint64_t c = 0;
+    for (int64_t i = 0; i < na; i++) {
+        int64_t lo = 0, hi = nb;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (b[mid] < a[i]) lo = mid + 1; else hi = mid;
+        }
+        if (lo < nb && b[lo] == a[i]) c++;
+    }
+    return c;
+}
+
+/* Triangle sums over the arcs (u, w) whose source u lies in [u_lo, u_hi):
+ *   *ffl = sum |N_out(u) ∩ N_in(w)|: the nodes x with u -> x -> w besides
+ *          u -> w, i.e. the feed-forward triangles whose source is in the
+ *          range; over all u this is sum(A o A^2);
+ *   *cyc = sum |N_out(w) ∩ N_in(u)|: the closed walks u -> w -> x -> u
+ *          starting with such an arc; over all u this is tr(A^3), three
+ *          times the number of directed 3-cycles.
+ * (No self-loops, so x differs from u and w in both sums.) */
+void og_triangle_sums(const og_graph *g, int32_t u_lo, int32_t u_hi, uint64_t *ffl, uint64_t *cyc) {
+    uint64_t f = 0, c = 0;
+    if (u_lo < 0) u_lo = 0;
+    if (u_hi > g->n) u_hi = g->n;
+    for (int32_t u = u_lo; u < u_hi; u++) {
+        const int32_t *ou = g->out_adj + g->out_off[u], *iu = g->in_adj + g->in_off[u];
+        const int64_t nou = g->out_off[u + 1] - g->out_off[u], niu = g->in_off[u + 1] - g->in_off[u];
+        for (int64_t j = 0; j < nou; j++) {
+            const int32_t w = ou[j];
+            f += common_ids(ou, nou, g->in_adj + g->in_off[w], g->in_off[w + 1] - g->in_off[w]);
+            c += common_ids(g->out_adj + g->out_off[w], g->out_off[w + 1] - g->out_off[w], iu, niu);
+        }
+    }
+    *ffl = f;
+    *cyc = c;
 }
 
 /* Replaces each k-tuple (an embedding written in pattern-vertex order) by the

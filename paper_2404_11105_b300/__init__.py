@@ -32,7 +32,8 @@ EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_gr
            "xm_query_bytes", "xm_server_create", "xm_server_submit", "xm_server_poll", "xm_server_info",
            "xm_server_free", "xm_count_roots", "xm_enumerate_roots", "xm_count_roots_stats", "xm_plan_tune",
            "xm_plan_product", "xm_plan_product_set", "xm_plan_split", "xm_plan_split_part",
-           "xm_plan_split_quotient"]
+           "xm_plan_split_quotient", "xm_count_roots_each", "xm_plan_tune_roots", "xm_fault_inject",
+           "xm_device_bytes_live"]
 
 
 class XmError(RuntimeError):
@@ -43,12 +44,14 @@ class XmError(RuntimeError):
 
 class xm_tuning(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int32), ("unit", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("budget_ms", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("budget_ms", ctypes.c_int32), ("merge_ratio", ctypes.c_int32)]
 
 
 class xm_stats(ctypes.Structure):
     _fields_ = [("alg_bytes", ctypes.c_uint64), ("extensions", ctypes.c_uint64), ("set_ops", ctypes.c_uint64),
-                ("units", ctypes.c_uint64), ("leaf_elems", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 3)]
+                ("units", ctypes.c_uint64), ("leaf_elems", ctypes.c_uint64), ("l1_bytes", ctypes.c_uint64),
+                ("touched_bytes", ctypes.c_uint64), ("warp_exit_first_ns", ctypes.c_uint64),
+                ("warp_exit_mean_ns", ctypes.c_uint64), ("warp_exit_last_ns", ctypes.c_uint64)]
 
 
 class xm_level_info(ctypes.Structure):
@@ -69,6 +72,8 @@ def _load():
         "xm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "xm_last_error": (ctypes.c_char_p, []),
         "xm_version": (ctypes.c_int, []),
+        "xm_fault_inject": (ctypes.c_int, [ctypes.c_char_p]),
+        "xm_device_bytes_live": (ctypes.c_uint64, []),
         "xm_load_graph": (ctypes.c_int, [i32, i64, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]),
         "xm_graph_info": (ctypes.c_int, [vp, i32p, ctypes.POINTER(i64)]),
         "xm_graph_csr": (ctypes.c_int, [vp] + [ctypes.POINTER(vp)] * 4),
@@ -106,9 +111,12 @@ def _load():
         "xm_count_batch": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64, i32p, u64p, vp]),
         "xm_query_bytes": (ctypes.c_uint64, [vp, vp]),
         "xm_count_roots": (ctypes.c_int, [vp, vp, i32p, i64, u64p, u64p, vp]),
+        "xm_count_roots_each": (ctypes.c_int, [vp, vp, i32p, i64, u64p, vp]),
         "xm_plan_tune": (ctypes.c_int, [vp, vp, ctypes.POINTER(xm_tuning), i32, i32, ctypes.POINTER(xm_tuning),
                                         ctypes.POINTER(ctypes.c_float), vp]),
         "xm_count_roots_stats": (ctypes.c_int, [vp, vp, i32p, i64, u64p, u64p, ctypes.POINTER(xm_stats), vp]),
+        "xm_plan_tune_roots": (ctypes.c_int, [vp, vp, i32p, i64, ctypes.POINTER(xm_tuning), i32, i32,
+                                              ctypes.POINTER(xm_tuning), ctypes.POINTER(ctypes.c_float), vp]),
         "xm_enumerate_roots": (ctypes.c_int, [vp, vp, i32p, i64, vp, ctypes.c_uint64, u64p, u64p, vp]),
         "xm_server_create": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.c_uint64, ctypes.POINTER(vp)]),
         "xm_server_submit": (ctypes.c_int, [vp, vp, i32, i64, i32p]),
@@ -274,8 +282,8 @@ class Plan:
         lib().xm_plan_describe(self._h, buf, need + 1)
         return buf.value.decode()
 
-    def set_tuning(self, window=0, unit=0, warps_per_block=0, blocks_per_sm=0, budget_ms=0):
-        t = xm_tuning(window, unit, warps_per_block, blocks_per_sm, budget_ms)
+    def set_tuning(self, window=0, unit=0, warps_per_block=0, blocks_per_sm=0, budget_ms=0, merge_ratio=0):
+        t = xm_tuning(window, unit, warps_per_block, blocks_per_sm, budget_ms, merge_ratio)
         _check(lib().xm_plan_set_tuning(self._h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
@@ -293,6 +301,16 @@ class Plan:
             self.free()
         except Exception:
             pass
+
+
+def fault_inject(spec: str):
+    """Host-side fault injection ("alloc:N", "compile:N", "none")."""
+    _check(lib().xm_fault_inject(spec.encode()))
+
+
+def device_bytes_live() -> int:
+    """Device bytes the library currently holds."""
+    return int(lib().xm_device_bytes_live())
 
 
 def xm_count(g: Graph, p: Plan, stream=None) -> int:
@@ -356,8 +374,8 @@ class Batch:
                                      pp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(h)))
         self._h = h
 
-    def set_tuning(self, window=0, unit=0, warps_per_block=0, blocks_per_sm=0, budget_ms=0):
-        t = xm_tuning(window, unit, warps_per_block, blocks_per_sm, budget_ms)
+    def set_tuning(self, window=0, unit=0, warps_per_block=0, blocks_per_sm=0, budget_ms=0, merge_ratio=0):
+        t = xm_tuning(window, unit, warps_per_block, blocks_per_sm, budget_ms, merge_ratio)
         _check(lib().xm_batch_set_tuning(self._h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
@@ -466,6 +484,15 @@ def xm_count_roots(g: Graph, p: Plan, roots, stream=None) -> int:
     return (hi.value << 64) | lo.value
 
 
+def xm_count_roots_each(g: Graph, p: Plan, roots, stream=None) -> list:
+    """Per-start-node counts, in the order of `roots` (host int array)."""
+    r = np.ascontiguousarray(roots, np.int32)
+    out = np.zeros(2 * max(len(r), 1), np.uint64)
+    _check(lib().xm_count_roots_each(g._h, p._h, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(r),
+                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _stream(stream)))
+    return [(int(out[2 * i + 1]) << 64) | int(out[2 * i]) for i in range(len(r))]
+
+
 def xm_enumerate_roots(g: Graph, p: Plan, roots, out, capacity: int | None = None, stream=None):
     r = np.ascontiguousarray(roots, np.int32)
     cap = out.numel() // p.k if capacity is None else capacity
@@ -486,11 +513,17 @@ def xm_count_roots_stats(g: Graph, p: Plan, roots, stream=None):
     return (hi.value << 64) | lo.value, {f: getattr(st, f) for f, _ in xm_stats._fields_ if f != "reserved"}
 
 
-def xm_plan_tune(g: Graph, p: Plan, candidates, reps: int = 2, stream=None):
-    """Autotune p's launch parameters on graph g; returns (best tuning, ms)."""
+def xm_plan_tune(g: Graph, p: Plan, candidates, reps: int = 2, roots=None, stream=None):
+    """Autotune p's launch parameters on graph g (on the counts of a
+    start-node list when `roots` is given); returns (best tuning, ms)."""
     arr = (xm_tuning * len(candidates))(*[xm_tuning(*c) for c in candidates])
     best = xm_tuning()
     ms = ctypes.c_float()
-    _check(lib().xm_plan_tune(g._h, p._h, arr, len(candidates), reps, ctypes.byref(best), ctypes.byref(ms),
-                              _stream(stream)))
+    if roots is None:
+        _check(lib().xm_plan_tune(g._h, p._h, arr, len(candidates), reps, ctypes.byref(best), ctypes.byref(ms),
+                                  _stream(stream)))
+    else:
+        r = np.ascontiguousarray(roots, np.int32)
+        _check(lib().xm_plan_tune_roots(g._h, p._h, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(r), arr,
+                                        len(candidates), reps, ctypes.byref(best), ctypes.byref(ms), _stream(stream)))
     return {f: getattr(best, f) for f, _ in xm_tuning._fields_}, ms.value

@@ -4,8 +4,10 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <new>
 #include <string>
 #include <vector>
@@ -19,6 +21,109 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+// ---------------------------------------------- device memory, fault hooks
+// Injected faults: the countdown-th next device allocation (or pattern
+// compile) fails; 0 = none. Set by xm_fault_inject or, when the library
+// loads, by the environment variable XM_FAULT ("alloc:N", "compile:N",
+// comma-separated).
+static std::mutex g_mem_mu;
+static std::unordered_map<void*, size_t> g_live;
+static uint64_t g_live_bytes = 0;
+static long long g_alloc_countdown = 0, g_compile_countdown = 0;
+
+static int parse_fault(const char* spec) {
+    if (!spec || !*spec) return XM_EINVAL;
+    std::string s(spec);
+    long long a = 0, c = 0;
+    size_t i = 0;
+    while (i < s.size()) {
+        size_t j = s.find(',', i);
+        if (j == std::string::npos) j = s.size();
+        const std::string item = s.substr(i, j - i);
+        const size_t colon = item.find(':');
+        const std::string kind = item.substr(0, colon);
+        long long nth = 0;
+        if (colon != std::string::npos) {
+            char* end = nullptr;
+            nth = std::strtoll(item.c_str() + colon + 1, &end, 10);
+            if (!end || *end || nth < 1) return XM_EINVAL;
+        }
+        if (kind == "alloc" && nth) a = nth;
+        else if (kind == "compile" && nth) c = nth;
+        else if (kind == "none" && colon == std::string::npos) a = c = 0;
+        else return XM_EINVAL;
+        i = j + 1;
+    }
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    g_alloc_countdown = a;
+    g_compile_countdown = c;
+    return XM_OK;
+}
+
+static const int g_env_fault = []() {
+    const char* e = std::getenv("XM_FAULT");
+    return e ? parse_fault(e) : XM_OK;
+}();
+
+static bool take_fault(long long& countdown) {
+    if (countdown <= 0) return false;
+    return --countdown == 0;
+}
+
+bool compile_fault() {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    return take_fault(g_compile_countdown);
+}
+
+cudaError_t dev_alloc_raw(void** p, size_t bytes) {
+    {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        if (take_fault(g_alloc_countdown)) return cudaErrorMemoryAllocation;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        g_live[*p] = bytes;
+        g_live_bytes += bytes;
+    }
+    return e;
+}
+
+cudaError_t dev_alloc_async_raw(void** p, size_t bytes, cudaStream_t stream) {
+    {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        if (take_fault(g_alloc_countdown)) return cudaErrorMemoryAllocation;
+    }
+    cudaError_t e = cudaMallocAsync(p, bytes, stream);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        g_live[*p] = bytes;
+        g_live_bytes += bytes;
+    }
+    return e;
+}
+
+static void forget(void* p) {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    auto it = g_live.find(p);
+    if (it != g_live.end()) {
+        g_live_bytes -= it->second;
+        g_live.erase(it);
+    }
+}
+
+void dev_free(void* p) {
+    if (!p) return;
+    forget(p);
+    cudaFree(p);
+}
+
+cudaError_t dev_free_async(void* p, cudaStream_t stream) {
+    if (!p) return cudaSuccess;
+    forget(p);
+    return cudaFreeAsync(p, stream);
+}
+
 static int cuda_fail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return XM_ECUDA;
@@ -30,7 +135,7 @@ static int cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-static const xm_tuning kDefaultTuning = {512, 32, 8, 0, 0};
+static const xm_tuning kDefaultTuning = {512, 32, 8, 0, 0, MERGE_RATIO_DEFAULT};
 
 static bool is_device_ptr(const void* p) {
     if (!p) return false;
@@ -44,24 +149,24 @@ static bool is_device_ptr(const void* p) {
 
 static void free_graph(xm_graph_s* g) {
     if (!g) return;
-    cudaFree(g->d_out_off);
-    cudaFree(g->d_out_adj);
-    cudaFree(g->d_in_off);
-    cudaFree(g->d_in_adj);
-    cudaFree(g->d_out_hoff);
-    cudaFree(g->d_out_htab);
-    cudaFree(g->d_in_hoff);
-    cudaFree(g->d_in_htab);
-    cudaFree(g->d_roots);
-    cudaFree(g->d_root_chunks);
-    cudaFree(g->d_chunk_cnt);
-    cudaFree(g->d_l1set);
-    cudaFree(g->d_units);
-    cudaFree(g->d_l1root);
-    cudaFree(g->d_e_units);
-    cudaFree(g->d_block_sums);
-    cudaFree(g->d_ctl);
-    cudaFree(g->d_root_counts);
+    dev_free(g->d_out_off);
+    dev_free(g->d_out_adj);
+    dev_free(g->d_in_off);
+    dev_free(g->d_in_adj);
+    dev_free(g->d_out_hoff);
+    dev_free(g->d_out_htab);
+    dev_free(g->d_in_hoff);
+    dev_free(g->d_in_htab);
+    dev_free(g->d_roots);
+    dev_free(g->d_root_chunks);
+    dev_free(g->d_chunk_cnt);
+    dev_free(g->d_l1set);
+    dev_free(g->d_units);
+    dev_free(g->d_l1root);
+    dev_free(g->d_e_units);
+    dev_free(g->d_block_sums);
+    dev_free(g->d_ctl);
+    dev_free(g->d_root_counts);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
     delete g;
@@ -113,6 +218,7 @@ static int run_plan(xm_graph g, const Plan& P, const xm_tuning& t, int mode, int
     a.capacity = capacity;
     a.budget_ns = (unsigned long long)t.budget_ms * 1000000ull;
     a.root_counts = root_counts;
+    a.merge_ratio = t.merge_ratio;
     XM_CUDA(cudaMemsetAsync(g->d_ctl, 0, CTL_WORDS * sizeof(unsigned long long), stream), "cudaMemsetAsync");
     XM_CUDA(cudaMemcpyAsync(ctl_plan(g), &P.dev, sizeof(XmPlanDev), cudaMemcpyHostToDevice, stream),
             "plan upload");
@@ -139,8 +245,16 @@ static int run_plan(xm_graph g, const Plan& P, const xm_tuning& t, int mode, int
         stats->set_ops = ctl[CTL_STATS + 2];
         stats->units = ctl[CTL_STATS + 3];
         stats->leaf_elems = ctl[CTL_STATS + 4];
-        // start-node degree checks: 16 B per node in range
-        stats->alg_bytes += 16ull * (uint64_t)(roots ? nroots : (int64_t)(a.r_hi - a.r_lo));
+        // the first-level pass, plus its start-node degree checks: 16 B per
+        // node in range
+        stats->l1_bytes = ctl[CTL_STATS + 5] + 16ull * (uint64_t)(roots ? nroots : (int64_t)(a.r_hi - a.r_lo));
+        stats->touched_bytes = ctl[CTL_STATS + 6];
+        const unsigned long long t0 = ctl[CTL_W_START];
+        if (t0 && ctl[CTL_W_COUNT]) {
+            stats->warp_exit_first_ns = ~ctl[CTL_W_FIRST] - t0;
+            stats->warp_exit_mean_ns = ctl[CTL_W_SUM] / ctl[CTL_W_COUNT];
+            stats->warp_exit_last_ns = ctl[CTL_W_LAST] - t0;
+        }
     }
     if (mode == MODE_EMIT && ctl[CTL_EMIT] > capacity) {
         set_error("enumeration buffer too small");
@@ -159,6 +273,23 @@ static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int3
 
 typedef unsigned __int128 u128;
 
+// The graph's per-node 128-bit counters (split parts, per-root counts):
+// at least `words` words, grown on demand.
+static int ensure_root_counts(xm_graph g, size_t words) {
+    if (g->root_count_words >= words) return XM_OK;
+    dev_free(g->d_root_counts);
+    g->d_root_counts = nullptr;
+    g->root_count_words = 0;
+    cudaError_t e = dev_alloc(&g->d_root_counts, words * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("per-node counters: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA;
+    }
+    g->root_count_words = words;
+    return XM_OK;
+}
+
 // Whole-graph count of plan P (matches, or embeddings with XM_EMBEDDINGS),
 // through its cut-vertex decomposition when it has one:
 //   emb(P) = part_factor * sum_v prod_i m_i(v) - sum_j mult_j * emb(Q_j)
@@ -174,13 +305,8 @@ static int count_plan(xm_graph g, const Plan& P, const xm_tuning& t, u128& resul
     }
     const int nparts = (int)d->parts.size();
     const size_t words = (size_t)nparts * 2 * (size_t)g->n + 2;
-    if (g->root_count_words < words) {
-        cudaFree(g->d_root_counts);
-        g->d_root_counts = nullptr;
-        g->root_count_words = 0;
-        XM_CUDA(cudaMalloc(&g->d_root_counts, words * sizeof(unsigned long long)), "per-node counters");
-        g->root_count_words = words;
-    }
+    int rc0 = ensure_root_counts(g, words);
+    if (rc0) return rc0;
     unsigned long long* cnt = g->d_root_counts;
     unsigned long long* sum = cnt + (size_t)nparts * 2 * g->n;
     XM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)nparts * 2 * g->n * sizeof(unsigned long long), stream), "memset");
@@ -228,7 +354,18 @@ const char* xm_strerror(int status) {
 
 const char* xm_last_error(void) { return g_last_error.c_str(); }
 
-int xm_version(void) { return 100; }
+int xm_version(void) { return 200; }
+
+int xm_fault_inject(const char* spec) {
+    int rc = parse_fault(spec);
+    if (rc) set_error("fault spec must be \"none\" or \"alloc:N\" / \"compile:N\" (N >= 1), comma-separated");
+    return rc;
+}
+
+uint64_t xm_device_bytes_live(void) {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    return g_live_bytes;
+}
 
 int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, int flags, void* stream_,
                   xm_graph* out) {
@@ -269,18 +406,18 @@ int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, 
         g->n_block_sums = (std::max<int64_t>(std::max<int64_t>((int64_t)n + 1, g->cmax + 1), H.m + 2) + SCAN_TILE - 1) /
                           SCAN_TILE;
         cudaError_t e = cudaSuccess;
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_out_off, off_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_in_off, off_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_out_adj, adj_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_in_adj, adj_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_root_chunks, off_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_chunk_cnt, (size_t)(g->cmax + 1) * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_l1set, adj_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_units, off_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_l1root, adj_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_e_units, adj_b + sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_block_sums, g->n_block_sums * sizeof(int64_t));
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_ctl, ctl_bytes());
+        if (e == cudaSuccess) e = dev_alloc(&g->d_out_off, off_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_in_off, off_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_out_adj, adj_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_in_adj, adj_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_root_chunks, off_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_chunk_cnt, (size_t)(g->cmax + 1) * sizeof(int32_t));
+        if (e == cudaSuccess) e = dev_alloc(&g->d_l1set, adj_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_units, off_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_l1root, adj_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_e_units, adj_b + sizeof(int32_t));
+        if (e == cudaSuccess) e = dev_alloc(&g->d_block_sums, g->n_block_sums * sizeof(int64_t));
+        if (e == cudaSuccess) e = dev_alloc(&g->d_ctl, ctl_bytes());
         for (auto& ev : g->ev)
             if (e == cudaSuccess) e = cudaEventCreate(&ev);
         if (e != cudaSuccess) {
@@ -302,10 +439,10 @@ int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, 
         }
         g->hash_slots = hoff_out[n] + hoff_in[n];
         const size_t hoff_b = ((size_t)n + 1) * sizeof(int64_t);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_out_hoff, hoff_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_in_hoff, hoff_b);
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_out_htab, (size_t)std::max<int64_t>(hoff_out[n], 1) * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&g->d_in_htab, (size_t)std::max<int64_t>(hoff_in[n], 1) * sizeof(int32_t));
+        if (e == cudaSuccess) e = dev_alloc(&g->d_out_hoff, hoff_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_in_hoff, hoff_b);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_out_htab, (size_t)std::max<int64_t>(hoff_out[n], 1) * sizeof(int32_t));
+        if (e == cudaSuccess) e = dev_alloc(&g->d_in_htab, (size_t)std::max<int64_t>(hoff_in[n], 1) * sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_out_hoff, hoff_out.data(), hoff_b, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_in_hoff, hoff_in.data(), hoff_b, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess && hoff_out[n])
@@ -361,6 +498,7 @@ int xm_graph_last_timing(xm_graph g, float* prep_ms, float* match_ms) {
 
 int xm_compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pdst, int flags, xm_plan* out) {
     if (!out) { set_error("NULL output handle"); return XM_EINVAL; }
+    if (compile_fault()) { set_error("injected fault: pattern compile"); return XM_ENOMEM; }
     try {
         xm_plan_s* p = new xm_plan_s();
         std::string err;
@@ -507,6 +645,11 @@ int xm_plan_set_tuning(xm_plan p, const xm_tuning* t) {
     if (v.warps_per_block < 1 || v.warps_per_block > 16) { set_error("warps_per_block must be in [1, 16]"); return XM_EINVAL; }
     if (v.blocks_per_sm < 0 || v.blocks_per_sm > 64) { set_error("blocks_per_sm must be in [0, 64]"); return XM_EINVAL; }
     if (v.budget_ms < 0) { set_error("budget_ms must be >= 0"); return XM_EINVAL; }
+    if (v.merge_ratio == 0) v.merge_ratio = MERGE_RATIO_DEFAULT;
+    if (v.merge_ratio != -1 && (v.merge_ratio < 1 || v.merge_ratio > 1024)) {
+        set_error("merge_ratio must be -1 or in [1, 1024] (0: default)");
+        return XM_EINVAL;
+    }
     p->tuning = v;
     return XM_OK;
 }
@@ -517,8 +660,26 @@ int xm_plan_get_tuning(xm_plan p, xm_tuning* t) {
     return XM_OK;
 }
 
+static int tune(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, const xm_tuning* cand, int32_t ncand,
+                int32_t reps, xm_tuning* best, float* best_ms, void* stream);
+
 int xm_plan_tune(xm_graph g, xm_plan p, const xm_tuning* cand, int32_t ncand, int32_t reps, xm_tuning* best,
                  float* best_ms, void* stream) {
+    return tune(g, p, nullptr, 0, cand, ncand, reps, best, best_ms, stream);
+}
+
+int xm_plan_tune_roots(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, const xm_tuning* cand,
+                       int32_t ncand, int32_t reps, xm_tuning* best, float* best_ms, void* stream) {
+    if (!roots) { set_error("NULL root list"); return XM_EINVAL; }
+    return tune(g, p, roots, nroots, cand, ncand, reps, best, best_ms, stream);
+}
+
+// The autotuner: each candidate runs the count once to warm up, then `reps`
+// times timed with the graph's events (first-level pass + matcher); the
+// fastest candidate is kept. On the whole graph (xm_count) or a root list
+// (xm_count_roots).
+static int tune(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, const xm_tuning* cand, int32_t ncand,
+                int32_t reps, xm_tuning* best, float* best_ms, void* stream) {
     if (!g || !p || !cand || ncand < 1 || reps < 1) { set_error("bad tuning arguments"); return XM_EINVAL; }
     const xm_tuning keep = p->tuning;
     float best_t = -1.0f;
@@ -530,7 +691,7 @@ int xm_plan_tune(xm_graph g, xm_plan p, const xm_tuning* cand, int32_t ncand, in
         float t_min = -1.0f;
         for (int r = 0; r <= reps; r++) {  // the first run warms up
             uint64_t lo = 0, hi = 0;
-            rc = xm_count(g, p, &lo, &hi, stream);
+            rc = roots ? xm_count_roots(g, p, roots, nroots, &lo, &hi, stream) : xm_count(g, p, &lo, &hi, stream);
             if (rc) { p->tuning = keep; return rc; }
             if (c == 0 && r == 0) { want_lo = lo; want_hi = hi; }
             if (lo != want_lo || hi != want_hi) {
@@ -583,12 +744,12 @@ static int stage_roots(xm_graph g, const int32_t* roots, int64_t nroots, int64_t
         if (v < 0 || v >= g->n) { set_error("root id outside [0, n)"); return XM_EINVAL; }
     std::sort(r.begin(), r.end());
     r.erase(std::unique(r.begin(), r.end()), r.end());
-    if (!g->d_roots) XM_CUDA(cudaMalloc(&g->d_roots, (size_t)g->n * sizeof(int32_t)), "root buffer");
+    if (!g->d_roots) XM_CUDA(dev_alloc(&g->d_roots, (size_t)g->n * sizeof(int32_t)), "root buffer");
     if (!r.empty())
         XM_CUDA(cudaMemcpyAsync(g->d_roots, r.data(), r.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream),
                 "root upload");
     XM_CUDA(cudaStreamSynchronize(stream), "root upload");
-    *kept = (int64_t)r.size();
+    if (kept) *kept = (int64_t)r.size();
     return XM_OK;
 }
 
@@ -601,6 +762,40 @@ int xm_count_roots(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, 
     if (kept == 0) { *lo = *hi = 0; return XM_OK; }
     return run(g, p, MODE_COUNT, 0, INT32_MAX, nullptr, 0, lo, hi, nullptr, nullptr, (cudaStream_t)stream, g->d_roots,
                kept);
+}
+
+int xm_count_roots_each(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, uint64_t* counts,
+                        void* stream_) {
+    if (!g || !p || (nroots > 0 && !counts)) { set_error("NULL argument"); return XM_EINVAL; }
+    if (!roots || nroots < 0) { set_error("bad root list"); return XM_EINVAL; }
+    cudaStream_t stream = (cudaStream_t)stream_;
+    for (int64_t i = 0; i < nroots; i++)
+        if (roots[i] < 0 || roots[i] >= g->n) { set_error("root id outside [0, n)"); return XM_EINVAL; }
+    // distinct roots, sorted; each caller entry maps to its position
+    std::vector<int32_t> r(roots, roots + nroots);
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    const int64_t kept = (int64_t)r.size();
+    if (kept == 0) return XM_OK;
+    int rc = stage_roots(g, r.data(), kept, nullptr, stream);
+    if (rc) return rc;
+    if ((rc = ensure_root_counts(g, 2 * (size_t)kept))) return rc;
+    XM_CUDA(cudaMemsetAsync(g->d_root_counts, 0, 2 * (size_t)kept * sizeof(unsigned long long), stream), "memset");
+    uint64_t lo = 0, hi = 0;
+    rc = run_plan(g, p->plan, p->tuning, MODE_COUNT, 0, INT32_MAX, nullptr, 0, &lo, &hi, nullptr, nullptr, stream,
+                  g->d_roots, kept, g->d_root_counts);
+    if (rc) return rc;
+    std::vector<uint64_t> per(2 * (size_t)kept);
+    XM_CUDA(cudaMemcpyAsync(per.data(), g->d_root_counts, per.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                            stream),
+            "per-root readback");
+    XM_CUDA(cudaStreamSynchronize(stream), "per-root readback");
+    for (int64_t i = 0; i < nroots; i++) {
+        const int64_t j = std::lower_bound(r.begin(), r.end(), roots[i]) - r.begin();
+        counts[2 * i] = per[2 * j];
+        counts[2 * i + 1] = per[2 * j + 1];
+    }
+    return XM_OK;
 }
 
 int xm_count_roots_stats(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, uint64_t* lo, uint64_t* hi,

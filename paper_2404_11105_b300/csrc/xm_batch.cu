@@ -16,7 +16,7 @@ struct xm_batch_s {
     int device = 0;
     int64_t npairs = 0;
     int kmax = 2;
-    xm_tuning tuning{256, 64, 8, 0, 0};
+    xm_tuning tuning{256, 64, 8, 0, 0, xm::MERGE_RATIO_DEFAULT};
     std::vector<int32_t> pair_n;  // start nodes of each pair's graph
     xm::GraphDev* d_graphs = nullptr;
     XmPlanDev* d_plans = nullptr;
@@ -48,12 +48,12 @@ void free_batch(xm_batch_s* b) {
     if (!b) return;
     drop_graph(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    cudaFree(b->d_graphs);
-    cudaFree(b->d_plans);
-    cudaFree(b->d_pairs);
-    cudaFree(b->d_prefix);
-    cudaFree(b->d_counts);
-    cudaFree(b->d_ctl);
+    dev_free(b->d_graphs);
+    dev_free(b->d_plans);
+    dev_free(b->d_pairs);
+    dev_free(b->d_prefix);
+    dev_free(b->d_counts);
+    dev_free(b->d_ctl);
     delete b;
 }
 
@@ -79,6 +79,7 @@ BatchDev descriptor(const xm_batch_s* b) {
     d.window = b->tuning.window;
     d.kmax = b->kmax;
     d.budget_ns = (unsigned long long)b->tuning.budget_ms * 1000000ull;
+    d.merge_ratio = b->tuning.merge_ratio;
     return d;
 }
 
@@ -145,12 +146,12 @@ int xm_batch_create(int32_t np, const xm_plan* plans, int32_t ng, const xm_graph
         hpairs[i] = make_int2(pi, gi);
         b->pair_n[i] = hg[gi].n;
     }
-    e = cudaMalloc(&b->d_graphs, ng * sizeof(GraphDev));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_plans, np * sizeof(XmPlanDev));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_pairs, npairs * sizeof(int2));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_prefix, (npairs + 1) * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, npairs * 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, CTL_WORDS * sizeof(unsigned long long));
+    e = dev_alloc(&b->d_graphs, ng * sizeof(GraphDev));
+    if (e == cudaSuccess) e = dev_alloc(&b->d_plans, np * sizeof(XmPlanDev));
+    if (e == cudaSuccess) e = dev_alloc(&b->d_pairs, npairs * sizeof(int2));
+    if (e == cudaSuccess) e = dev_alloc(&b->d_prefix, (npairs + 1) * sizeof(long long));
+    if (e == cudaSuccess) e = dev_alloc(&b->d_counts, npairs * 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_alloc(&b->d_ctl, CTL_WORDS * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_graphs, hg.data(), ng * sizeof(GraphDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_plans, hp.data(), np * sizeof(XmPlanDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_pairs, hpairs.data(), npairs * sizeof(int2), cudaMemcpyHostToDevice);
@@ -180,6 +181,11 @@ int xm_batch_set_tuning(xm_batch b, const xm_tuning* t) {
     if (v.warps_per_block < 1 || v.warps_per_block > 16) { set_error("warps_per_block must be in [1, 16]"); return XM_EINVAL; }
     if (v.blocks_per_sm < 0 || v.blocks_per_sm > 64) { set_error("blocks_per_sm must be in [0, 64]"); return XM_EINVAL; }
     if (v.budget_ms < 0) { set_error("budget_ms must be >= 0"); return XM_EINVAL; }
+    if (v.merge_ratio == 0) v.merge_ratio = MERGE_RATIO_DEFAULT;
+    if (v.merge_ratio != -1 && (v.merge_ratio < 1 || v.merge_ratio > 1024)) {
+        set_error("merge_ratio must be -1 or in [1, 1024] (0: default)");
+        return XM_EINVAL;
+    }
     int rc = check_device(b);
     if (rc) return rc;
     if (v.unit != b->tuning.unit && (rc = upload_prefix(b, v.unit))) return rc;

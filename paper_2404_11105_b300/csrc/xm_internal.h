@@ -79,6 +79,24 @@ int build_host_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
 
 void set_error(const std::string& msg);
 
+// Every device allocation of the library goes through these: they keep a
+// count of the bytes the library holds (xm_device_bytes_live) and let tests
+// make a chosen allocation fail (xm_fault_inject) without touching the GPU.
+cudaError_t dev_alloc_raw(void** p, size_t bytes);
+void dev_free(void* p);
+cudaError_t dev_alloc_async_raw(void** p, size_t bytes, cudaStream_t stream);
+cudaError_t dev_free_async(void* p, cudaStream_t stream);
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+    return dev_alloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+cudaError_t dev_alloc_async(T** p, size_t bytes, cudaStream_t stream) {
+    return dev_alloc_async_raw(reinterpret_cast<void**>(p), bytes, stream);
+}
+// true when an injected fault makes this pattern compile fail
+bool compile_fault();
+
 }  // namespace xm
 
 struct xm_plan_s {

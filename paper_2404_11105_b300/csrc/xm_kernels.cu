@@ -108,6 +108,7 @@ struct LvState {
 // (the layout is cut to the plan's size so that more of the SM's on-chip
 // memory stays L1 cache); never index st[] at or beyond k.
 struct WarpSmem {
+    int32_t* mtile;  // this warp's MERGE_TILE-id tile for merge intersections
     int32_t m[XM_MAXK];
     LvState st[XM_MAXK];
 };
@@ -123,13 +124,26 @@ __host__ __device__ constexpr size_t warp_state_bytes(int k) {
 }
 
 __host__ __device__ size_t batch_warp_bytes_impl(int kmax, int window) {
-    return plan_bytes(kmax) + warp_state_bytes(kmax) + (size_t)(kmax > 2 ? kmax - 2 : 0) * window * sizeof(int32_t);
+    return plan_bytes(kmax) + warp_state_bytes(kmax) + (size_t)(kmax > 2 ? kmax - 2 : 0) * window * sizeof(int32_t) +
+           MERGE_TILE * sizeof(int32_t);
 }
 
 
 __host__ __device__ constexpr int n_windows(int k) { return k > 3 ? k - 3 : 0; }
 
+// Per-warp shared memory of k_match: level state, windows of levels
+// 2..k-2, and the merge tile.
+__host__ __device__ constexpr size_t match_warp_bytes(int k, int window) {
+    return warp_state_bytes(k) + (size_t)n_windows(k) * window * sizeof(int32_t) + MERGE_TILE * sizeof(int32_t);
+}
 
+
+
+// Sum of a 32-bit value over the warp (every lane gets the total).
+__device__ __forceinline__ unsigned warp_sum(unsigned v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
 
 __device__ __forceinline__ int32_t ld(const int32_t* p, int i, bool shared) {
     return shared ? p[i] : __ldg(p + i);
@@ -142,6 +156,55 @@ __device__ __forceinline__ int lbound(const int32_t* p, int lo, int hi, int32_t 
         if (ld(p, mid, shared) < x) lo = mid + 1; else hi = mid;
     }
     return lo;
+}
+
+// Warp-cooperative lower bounds on a sorted list: the first index in
+// [lo, hi) with p[idx] >= x, computed by all 32 lanes together (every lane
+// gets the same result). Each round the lanes read 32 evenly spaced ids of
+// the remaining range and one ballot narrows it 32-fold, so a list of L ids
+// costs about log32(L) + 1 dependent reads instead of log2(L) for one
+// thread. warp_lbound2 runs two searches (x0 over [lo0, hi0), x1 over
+// [lo1, hi1)) in the same rounds, two independent reads per lane.
+__device__ __forceinline__ int warp_lbound(const int32_t* p, int lo, int hi, int32_t x, bool shared, int lane) {
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) >> 5;
+        const int q = lo + lane * step;
+        const bool lt = q < hi && ld(p, q, shared) < x;
+        const int c = __popc(__ballot_sync(FULL, lt));
+        if (c == 0) return lo;
+        const int nlo = lo + (c - 1) * step + 1;
+        hi = min(hi, lo + c * step);
+        lo = nlo;
+    }
+    const bool lt = lo + lane < hi && ld(p, lo + lane, shared) < x;
+    return lo + __popc(__ballot_sync(FULL, lt));
+}
+
+__device__ __forceinline__ void warp_lbound2(const int32_t* p, int lo0, int hi0, int32_t x0, int lo1, int hi1,
+                                             int32_t x1, int& r0, int& r1, int lane) {
+    bool d0 = false, d1 = false;
+    for (;;) {
+        const bool w0 = !d0 && hi0 - lo0 > 32, w1 = !d1 && hi1 - lo1 > 32;
+        if (!w0 && !w1) break;
+        const int s0 = (hi0 - lo0 + 31) >> 5, s1 = (hi1 - lo1 + 31) >> 5;
+        const int q0 = lo0 + lane * s0, q1 = lo1 + lane * s1;
+        const int32_t v0 = (w0 && q0 < hi0) ? __ldg(p + q0) : INT_MAX;
+        const int32_t v1 = (w1 && q1 < hi1) ? __ldg(p + q1) : INT_MAX;
+        const int c0 = __popc(__ballot_sync(FULL, v0 < x0));
+        const int c1 = __popc(__ballot_sync(FULL, v1 < x1));
+        if (w0) {
+            if (c0 == 0) { hi0 = lo0; d0 = true; }
+            else { const int nlo = lo0 + (c0 - 1) * s0 + 1; hi0 = min(hi0, lo0 + c0 * s0); lo0 = nlo; }
+        }
+        if (w1) {
+            if (c1 == 0) { hi1 = lo1; d1 = true; }
+            else { const int nlo = lo1 + (c1 - 1) * s1 + 1; hi1 = min(hi1, lo1 + c1 * s1); lo1 = nlo; }
+        }
+    }
+    const int32_t v0 = lo0 + lane < hi0 ? __ldg(p + lo0 + lane) : INT_MAX;
+    const int32_t v1 = lo1 + lane < hi1 ? __ldg(p + lo1 + lane) : INT_MAX;
+    r0 = lo0 + __popc(__ballot_sync(FULL, v0 < x0));
+    r1 = lo1 + __popc(__ballot_sync(FULL, v1 < x1));
 }
 
 __device__ __forceinline__ ListRef op_list(const GraphDev& g, int dir, int32_t v) {
@@ -362,7 +425,11 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
         int cnt = 0;
         int32_t* out = WRITE ? ra.l1set + ra.chunk_cnt[c] : nullptr;
         const bool filtered = no || L1.ndiff || (filter_deg && (L1.dout_min > 0 || L1.din_min > 0));
-        if (!filtered && MODE != MODE_STATS) {
+        // MODE_STATS (count pass only) adds the bytes of both passes: the
+        // driver range and probes once, 8 B per degree check, 8 B per
+        // candidate written with its owner, the offsets with a node's first
+        // chunk
+        if (!filtered) {
             // every driver id survives: count without reading, or copy
             if (WRITE) {
                 int32_t* own = ra.l1root + (out - ra.l1set);
@@ -372,6 +439,7 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
                 }
             } else if (lane == 0) {
                 ra.chunk_cnt[c] = end - pos;
+                if (MODE == MODE_STATS) st_bytes += (j == 0 ? 8ull : 0ull) + 12ull * (end - pos);
             }
             continue;
         }
@@ -379,7 +447,6 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
             const int run = end - pos;
             st_bytes += (j == 0 ? 8ull * (1 + no) : 0) + 4ull * run;
             if (no) st_bytes += 4ull * min((long long)o.len, (long long)run * ceil_log2p1(o.len));
-            if (filter_deg) st_bytes += 8ull * run;
         }
         for (; pos < end; pos += 32) {
             const int i = pos + lane;
@@ -395,6 +462,10 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
                     plo = __shfl_sync(FULL, q, min(31, end - 1 - pos));
                 }
             }
+            if (MODE == MODE_STATS && filter_deg && (L1.dout_min > 0 || L1.din_min > 0)) {
+                const int checks = __popc(__ballot_sync(FULL, ok));
+                if (lane == 0) st_bytes += 8ull * checks;
+            }
             if (ok && filter_deg) ok = passes_degree(g, x, L1.dout_min, L1.din_min);
             if (ok && L1.ndiff) ok = passes_diffs(L1, g, &v, x);
             const unsigned mask = __ballot_sync(FULL, ok);
@@ -405,10 +476,13 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
             }
             cnt += __popc(mask);
         }
-        if (!WRITE && lane == 0) ra.chunk_cnt[c] = cnt;
+        if (!WRITE && lane == 0) {
+            ra.chunk_cnt[c] = cnt;
+            if (MODE == MODE_STATS) st_bytes += 8ull * cnt;
+        }
     }
     }
-    if (MODE == MODE_STATS && !WRITE && lane == 0 && st_bytes) atomicAdd(ra.ctl + CTL_STATS + 0, st_bytes);
+    if (MODE == MODE_STATS && !WRITE && lane == 0 && st_bytes) atomicAdd(ra.ctl + CTL_STATS + 5, st_bytes);
 }
 
 // Work units per start node: its first-level set cut into `unit` pieces.
@@ -424,13 +498,135 @@ __global__ void k_units(RunArgs ra) {
     }
 }
 
+// ------------------------------------------------------ merge intersection
+// Two sorted lists of similar length are intersected by streaming both
+// (Alg. 2's A^{e.dest} cap Pi A^e when no list is much shorter than the
+// other): every id is read once, in coalesced 16-byte loads, instead of one
+// random hash-bucket sector per id of the shorter list.
+
+// Lane's MERGE_V ids of the tile of list p that starts at the 16-byte
+// boundary at or below position pos; *t0 receives the tile's first position.
+// Ids at positions before pos read as -1 and at or after end as INT_MAX, so
+// they sort before / after every node id and match nothing real. A 16-byte
+// chunk that holds a position in [pos, end) lies inside the page of that
+// position, so it is read whole; chunks entirely past end are not read.
+__device__ __forceinline__ int4 merge_tile(const int32_t* p, int pos, int end, int lane, int& t0) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p + pos);
+    t0 = pos - (int)((a & 15) >> 2);
+    const int q = t0 + 4 * lane;
+    int4 v = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+    if (q < end) v = __ldg(reinterpret_cast<const int4*>(a & ~uintptr_t(15)) + lane);
+    if (q < pos) v.x = -1;
+    if (q + 1 < pos) v.y = -1;
+    if (q + 2 < pos) v.z = -1;
+    if (q + 1 >= end) v.y = INT_MAX;
+    if (q + 2 >= end) v.z = INT_MAX;
+    if (q + 3 >= end) v.w = INT_MAX;
+    return v;
+}
+
+__device__ __forceinline__ int32_t int4_at(const int4& v, int j) {
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// Number of ids common to the ascending lists A[pa, ea) and B[pb, eb),
+// leaving out the matched nodes m[j] for the bits j of neq (injectivity).
+// Returns this lane's share; the warp's sum is the count. A should be the
+// shorter list. Each round loads one MERGE_TILE-id tile of each list, puts
+// B's into `tile` (shared memory, MERGE_TILE ints of this warp), looks every
+// id of A's tile up in it by binary search, and then advances both lists past
+// the smaller of the two tiles' last ids (one tile is always used up): the
+// merge-path step. Rounds re-read the unused rest of the other tile, which is
+// then in L1.
+__device__ unsigned merge_count(const int32_t* __restrict__ A, int pa, int ea, const int32_t* __restrict__ B, int pb,
+                                int eb, int32_t* tile, uint32_t neq, const int32_t* m, int lane) {
+    unsigned cnt = 0;
+    while (pa < ea && pb < eb) {
+        int ta, tb;
+        const int4 va = merge_tile(A, pa, ea, lane, ta);
+        const int4 vb = merge_tile(B, pb, eb, lane, tb);
+        __syncwarp();
+        reinterpret_cast<int4*>(tile)[lane] = vb;
+        __syncwarp();
+        const int la = min(ea, ta + MERGE_TILE) - 1 - ta;  // tile index of A's last real id
+        const int lb = min(eb, tb + MERGE_TILE) - 1 - tb;
+        const int32_t lastA = __shfl_sync(FULL, int4_at(va, la & 3), la >> 2);
+        const int32_t lim = min(lastA, tile[lb]);
+        int na = 0, nb = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int32_t x = int4_at(va, j), y = int4_at(vb, j);
+            const bool ok = x >= 0 && x <= lim;
+            na += __popc(__ballot_sync(FULL, ok));
+            nb += __popc(__ballot_sync(FULL, y >= 0 && y <= lim));
+            if (ok) {
+                int i = 0;  // number of tile ids below x (at most MERGE_TILE - 1)
+#pragma unroll
+                for (int s = MERGE_TILE / 2; s > 0; s >>= 1)
+                    if (tile[i + s - 1] < x) i += s;
+                bool f = tile[i] == x;
+                for (uint32_t nm = neq; nm && f; nm &= nm - 1) f = x != m[__ffs(nm) - 1];
+                cnt += f ? 1u : 0u;
+            }
+        }
+        pa += na;
+        pb += nb;
+    }
+    return cnt;
+}
+
 // ----------------------------------------------------------------- k_match
 
-// Sets up level l >= 2 for the partial match in ws.m[0..l-1]: operand lists
-// (or a complete earlier set in their place), driver, probes and the cut of
-// the driver by the order bounds. Returns algorithmic bytes (stats).
+// Work and traffic counters of the instrumented (MODE_STATS) kernel, which
+// takes exactly the code paths of the counting kernel.
+//   bytes    algorithmic bytes: per list operand 8 B of offsets; 4 B per id
+//            of a driver range scanned; for every other list the cheaper of
+//            scanning it or probing it once per driver id by binary search,
+//            4 B x min(|L|, run x ceil(log2(|L| + 1))), with |L| cut to the
+//            driver range's ids where the kernel computes that cut; a bound
+//            search in a list of L ids 4 B x ceil(log2(L + 1)); 8 B per
+//            degree check.
+//   touched  the bytes the kernel's chosen strategy moves at 32-byte-sector
+//            granularity if nothing were cached: a merge both ranges, a
+//            hash probe one sector, a binary search one sector per step
+//            above the last sector, a list's offsets one sector.
+struct Stats {
+    unsigned long long bytes = 0, touched = 0, ext = 0, sets = 0, units = 0, leaf = 0;
+};
+
+__device__ __forceinline__ unsigned long long search_bytes(int len) { return 4ull * ceil_log2p1(len); }
+__device__ __forceinline__ unsigned long long search_sectors(int len) {
+    return (unsigned long long)max(1, ceil_log2p1(len) - 3);
+}
+__device__ __forceinline__ unsigned long long probe_bytes(long long cut_len, long long run, int len) {
+    return 4ull * (unsigned long long)min(cut_len, run * ceil_log2p1(len));
+}
+
+// MODE_STATS, lane 0: a scan of `run` driver ids of set S against its probe
+// lists (probe 0 cut to cut0 ids when cut0 >= 0).
 template <int MODE>
-__device__ unsigned long long setup_lists(const XmLevel& L, const GraphDev& g, WarpSmem& ws, LvState& S, int lane) {
+__device__ __forceinline__ void account_scan(const LvState& S, long long run, Stats& st, int lane, long long cut0 = -1) {
+    if (MODE != MODE_STATS || lane != 0 || run <= 0) return;
+    if (!S.drv_shared) {
+        st.bytes += 4ull * run;
+        st.touched += 4ull * run;
+    }
+    for (int p = 0; p < S.nprobe; p++) {
+        if ((S.probe_shared >> p) & 1) continue;
+        const int len = S.phi[p];
+        st.bytes += probe_bytes(p == 0 && cut0 >= 0 ? cut0 : len, run, len);
+        st.touched += 32ull * run * (S.pT[p] ? 1ull : search_sectors(len));
+    }
+}
+
+// Sets up level record L for the partial match in ws.m: operand lists (or a
+// complete earlier set in their place), driver (the first shortest list),
+// probes and the cut of the driver by the order bounds. MODE_STATS adds the
+// offsets and bound searches to st, and with `whole` the scan of the whole
+// cut range (levels that are always scanned whole).
+template <int MODE>
+__device__ void setup_lists(const XmLevel& L, const GraphDev& g, WarpSmem& ws, LvState& S, int lane, Stats& st,
+                            bool whole) {
     int32_t lo, hi;
     level_bounds(L, ws.m, lo, hi);
     ListRef lists[XM_MAXOPS + 1];
@@ -467,11 +663,10 @@ __device__ unsigned long long setup_lists(const XmLevel& L, const GraphDev& g, W
     }
     int c0 = 0, c1 = lists[d].len;
     if (!empty) {
-        if (lo >= 0) c0 = lbound(lists[d].p, 0, c1, lo + 1, lists[d].shared);
-        if (hi != INT_MAX) c1 = lbound(lists[d].p, c0, c1, hi, lists[d].shared);
+        if (lo >= 0) c0 = warp_lbound(lists[d].p, 0, c1, lo + 1, lists[d].shared, lane);
+        if (hi != INT_MAX) c1 = warp_lbound(lists[d].p, c0, c1, hi, lists[d].shared, lane);
     }
     if (c0 >= c1) empty = true;
-    unsigned long long bytes = 0;
     if (lane == 0) {
         S.drv = lists[d].p;
         S.drv_shared = lists[d].shared;
@@ -496,25 +691,26 @@ __device__ unsigned long long setup_lists(const XmLevel& L, const GraphDev& g, W
         S.complete = 0;
         S.wcnt = S.wpos = S.it_hi = 0;
         if (MODE == MODE_STATS) {
-            const int run = empty ? 0 : c1 - c0;
             for (int i = 0; i < cnt; i++) {
                 if (lists[i].shared) continue;
-                bytes += 8;
-                if (empty) continue;
-                if (i == d) bytes += 4ull * run;
-                else if (lists[i].T) bytes += 4ull * min((long long)lists[i].len, (long long)run);
-                else bytes += 4ull * min((long long)lists[i].len, (long long)run * ceil_log2p1(lists[i].len));
+                st.bytes += 8;
+                st.touched += 32;
+            }
+            if (!lists[d].shared && lists[d].len > 0) {
+                const int nsearch = (lo >= 0 ? 1 : 0) + (hi != INT_MAX ? 1 : 0);
+                st.bytes += nsearch * search_bytes(lists[d].len);
+                st.touched += 32ull * nsearch * search_sectors(lists[d].len);
             }
         }
     }
     __syncwarp();
-    return bytes;
+    if (whole && !empty) account_scan<MODE>(S, c1 - c0, st, lane);
 }
 
 template <int MODE>
-__device__ __forceinline__ unsigned long long setup_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l,
-                                                          int lane) {
-    return setup_lists<MODE>(P.lv[l], g, ws, ws.st[l], lane);
+__device__ __forceinline__ void setup_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane,
+                                            Stats& st, bool whole) {
+    setup_lists<MODE>(P.lv[l], g, ws, ws.st[l], lane, st, whole);
 }
 
 // Runs the driver range [drv_pos, drv_end) of level l through probes and
@@ -524,7 +720,7 @@ __device__ __forceinline__ unsigned long long setup_level(const XmPlanDev& P, co
 template <int MODE, bool WINDOW>
 __device__ unsigned long long scan_level(const XmPlanDev& P, const XmLevel& L, const GraphDev& g, WarpSmem& ws,
                                          LvState& S, int l, int32_t* win, int W, int lane, const RunArgs& ra,
-                                         unsigned long long& stat_bytes) {
+                                         Stats& st) {
     const bool dsh = S.drv_shared;
     const int np = S.nprobe;
     int32_t plo[XM_MAXOPS];
@@ -558,13 +754,21 @@ __device__ unsigned long long scan_level(const XmPlanDev& P, const XmLevel& L, c
                 if (x == ws.m[__ffs(nm) - 1]) ok = false;
         }
         if (ok && L.ndiff) ok = passes_diffs(L, g, ws.m, x);
-        if (WINDOW && ok) ok = passes_degree(g, x, L.dout_min, L.din_min);
+        if (WINDOW) {
+            if (MODE == MODE_STATS && (L.dout_min > 0 || L.din_min > 0)) {
+                const int checks = __popc(__ballot_sync(FULL, ok));
+                if (lane == 0) {
+                    st.bytes += 8ull * checks;
+                    st.touched += 32ull * checks;
+                }
+            }
+            if (ok) ok = passes_degree(g, x, L.dout_min, L.din_min);
+        }
         const unsigned mask = __ballot_sync(FULL, ok);
         const int rank = __popc(mask & ((1u << lane) - 1));
         if (WINDOW) {
             if (ok) win[wcnt + rank] = x;
             wcnt += __popc(mask);
-            if (MODE == MODE_STATS && lane == 0) stat_bytes += 8ull * min(32, end - pos);
         } else if (MODE == MODE_EMIT) {
             const int c = __popc(mask);
             unsigned long long base = 0;
@@ -595,12 +799,12 @@ __device__ unsigned long long scan_level(const XmPlanDev& P, const XmLevel& L, c
 // Last-level count when every probe list has a hash table: 128 driver ids
 // per iteration (four per lane) with all four first-bucket probes issued
 // before any is checked, so four sector reads per lane are in flight.
-__device__ unsigned long long leaf_count_hashed(const XmLevel& L, WarpSmem& ws, LvState& S, int lane) {
+__device__ unsigned long long leaf_count_hashed(const XmLevel& L, WarpSmem& ws, LvState& S, int pos, int end,
+                                                int lane) {
     const bool dsh = S.drv_shared;
     const int np = S.nprobe;
-    const int end = S.drv_end;
     unsigned long long cnt = 0;
-    for (int pos = S.drv_pos; pos < end; pos += 128) {
+    for (; pos < end; pos += 128) {
         int32_t x[4];
         bool ok[4];
 #pragma unroll
@@ -633,11 +837,14 @@ __device__ unsigned long long leaf_count_hashed(const XmLevel& L, WarpSmem& ws, 
 
 // Count (or emit) the candidates of level l's set S, already set up from
 // record L, over the driver range [pos, end). The count is on lane 0.
+// Counting with two lists (driver and one probe, no difference lists): the
+// probe list is cut to the driver range's ids; when that cut is at most
+// ra.merge_ratio times the driver range both are merged, else the driver's
+// ids probe the list's hash table.
 template <int MODE>
 __device__ unsigned long long leaf_tail(const XmPlanDev& P, const XmLevel& L, const GraphDev& g, WarpSmem& ws,
-                                        LvState& S, int l, int lane, const RunArgs& ra, unsigned long long& stat_bytes,
-                                        unsigned long long& leaf_elems, int pos, int end) {
-    if (MODE == MODE_STATS && lane == 0) leaf_elems += end - pos;
+                                        LvState& S, int l, int lane, const RunArgs& ra, Stats& st, int pos, int end) {
+    if (MODE == MODE_STATS && lane == 0) st.leaf += end - pos;
     if (MODE != MODE_EMIT && S.nprobe == 0 && L.ndiff == 0) {
         // A single list: its size, minus already matched nodes inside it.
         unsigned long long c = end - pos;
@@ -645,36 +852,244 @@ __device__ unsigned long long leaf_tail(const XmPlanDev& P, const XmLevel& L, co
             const int32_t y = ws.m[__ffs(nm) - 1];
             const int q = lbound(S.drv, pos, end, y, S.drv_shared);
             if (q < end && ld(S.drv, q, S.drv_shared) == y) c--;
+            if (MODE == MODE_STATS && lane == 0 && !S.drv_shared) {
+                st.bytes += search_bytes(end - pos);
+                st.touched += 32ull * search_sectors(end - pos);
+            }
         }
         return lane == 0 ? c : 0;
     }
-    if (MODE == MODE_COUNT && L.ndiff == 0) {
-        bool hashed = S.probe_shared == 0;
+    const long long run = end - pos;
+    if (MODE != MODE_EMIT && L.ndiff == 0) {
+        const bool global = !S.drv_shared && S.probe_shared == 0;
+        long long cut0 = -1;
+        if (MODE == MODE_STATS && S.nprobe == 1 && global) {
+            // accounting only: the probe list cut to the driver range's ids
+            int pb, eb;
+            warp_lbound2(S.probe[0], 0, S.phi[0], __ldg(S.drv + pos), 0, S.phi[0], __ldg(S.drv + end - 1) + 1, pb,
+                         eb, lane);
+            cut0 = eb - pb;
+        }
+        if (S.nprobe == 1 && global && ra.merge_ratio > 0 && run >= MERGE_MIN_RUN &&
+            (long long)S.phi[0] <= (long long)ra.merge_ratio * run) {
+            // the whole probe list is within the ratio: merged whole, no cut
+            if (MODE == MODE_STATS && lane == 0) {
+                st.bytes += 4ull * run + probe_bytes(cut0, run, S.phi[0]);
+                st.touched += 4ull * (run + S.phi[0]) + 64;
+            }
+            unsigned c = merge_count(S.drv, pos, end, S.probe[0], 0, S.phi[0], ws.mtile, L.neq_mask, ws.m, lane);
+            c = warp_sum(c);
+            return lane == 0 ? c : 0;
+        }
+        account_scan<MODE>(S, run, st, lane, cut0);
+        bool hashed = global;
         for (int p = 0; p < S.nprobe && hashed; p++) hashed = S.pT[p] != 0;
-        if (hashed) return leaf_count_hashed(L, ws, S, lane);
+        if (hashed) return leaf_count_hashed(L, ws, S, pos, end, lane);
+    } else {
+        account_scan<MODE>(S, run, st, lane);
     }
-    unsigned long long r = scan_level<MODE, false>(P, L, g, ws, S, l, nullptr, 0, lane, ra, stat_bytes);
-    return lane == 0 ? r : 0;
-}
-
-// Count (or emit) the candidates of the last level l >= 2.
-template <int MODE>
-__device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane,
-                                         const RunArgs& ra, unsigned long long& stat_bytes,
-                                         unsigned long long& leaf_elems, int ra_pos = 0, int ra_len = -1) {
-    stat_bytes += setup_level<MODE>(P, g, ws, l, lane);
-    LvState& S = ws.st[l];
-    if (S.empty) return 0;
-    // optional sub-range [c0 + ra_pos, c0 + ra_pos + ra_len) of the cut driver range
-    const int pos = ra_len < 0 ? S.c0 : min(S.c1, S.c0 + ra_pos);
-    const int end = ra_len < 0 ? S.c1 : min(S.c1, pos + ra_len);
-    if (pos >= end) return 0;
-    if (ra_len >= 0 && lane == 0) {
+    if (lane == 0) {
         S.drv_pos = pos;
         S.drv_end = end;
     }
     __syncwarp();
-    return leaf_tail<MODE>(P, P.lv[l], g, ws, S, l, lane, ra, stat_bytes, leaf_elems, pos, end);
+    unsigned long long r = scan_level<MODE, false>(P, L, g, ws, S, l, nullptr, 0, lane, ra, st);
+    return lane == 0 ? r : 0;
+}
+
+// Count (or emit) the candidates of the last level l >= 2, optionally only
+// the sub-range [c0 + ra_pos, c0 + ra_pos + ra_len) of its cut driver range.
+template <int MODE>
+__device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane,
+                                         const RunArgs& ra, Stats& st, int ra_pos = 0, int ra_len = -1) {
+    setup_level<MODE>(P, g, ws, l, lane, st, false);
+    LvState& S = ws.st[l];
+    if (S.empty) return 0;
+    const int pos = ra_len < 0 ? S.c0 : min(S.c1, S.c0 + ra_pos);
+    const int end = ra_len < 0 ? S.c1 : min(S.c1, pos + ra_len);
+    if (pos >= end) return 0;
+    return leaf_tail<MODE>(P, P.lv[l], g, ws, S, l, lane, ra, st, pos, end);
+}
+
+// Plans whose last level k - 1 intersects exactly two operand lists, one of
+// a level before k - 2 (F, the same for every candidate of level k - 2) and
+// one of level k - 2 itself (V, each candidate's own list), with no reuse and
+// no difference lists, count their last level a batch of level-(k-2)
+// candidates at a time (leaf_batch). Returns F's operand index, or -1.
+__host__ __device__ inline int batch_leaf_fixed_op(const XmPlanDev& P) {
+    if (P.k < 4) return -1;
+    const XmLevel& L = P.lv[P.k - 1];
+    const int l = P.k - 2;
+    if (L.nops != 2 || L.ndiff != 0 || L.reuse >= 1) return -1;
+    const bool v0 = L.op_level[0] == l, v1 = L.op_level[1] == l;
+    if (v0 == v1) return -1;
+    return v0 ? 1 : 0;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ const T* shfl_ptr(const T* p, int src) {
+    return reinterpret_cast<const T*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(p), src));
+}
+
+// The last level k - 1 of the nb <= 32 partial matches m_0..m_{l-1}, x_i
+// (l = k - 2; lane i holds candidate x_i = cand[i]): each counts |F cap
+// V(x_i)| within the order bounds, minus matched nodes, F being the batch's
+// common operand list (cut once per batch) and V(x_i) lane i's own list (cut
+// per lane). Pairs whose shorter range has at least MERGE_MIN_RUN ids and
+// whose longer range is at most ra.merge_ratio times as long are merged, one
+// pair at a time by the whole warp. The other pairs are counted together:
+// the ids of their shorter ranges form one flattened index space that the
+// lanes walk 128 ids per round (four per lane), each id probing the other
+// list of its own pair (its hash table, or a binary search in a list too
+// short for one), so a warp keeps 128 probes in flight however the ids are
+// spread over the pairs. Returns the lane's share of the count.
+template <int MODE>
+__device__ unsigned long long leaf_batch(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int iF,
+                                         const int32_t* cand, bool cand_shared, int nb, int lane, const RunArgs& ra,
+                                         Stats& st) {
+    const int l = P.k - 2;
+    const XmLevel& L = P.lv[P.k - 1];
+    const int iV = 1 - iF;
+    const uint32_t below = (1u << l) - 1;
+    // the common list F and the order bounds of levels before l
+    const ListRef F = op_list(g, L.op_dir[iF], ws.m[L.op_level[iF]]);
+    int32_t lo = -1, hi = INT_MAX;
+    for (uint32_t a = L.lo_mask & below; a; a &= a - 1) lo = max(lo, ws.m[__ffs(a) - 1]);
+    for (uint32_t b = L.hi_mask & below; b; b &= b - 1) hi = min(hi, ws.m[__ffs(b) - 1]);
+    int f0 = 0, f1 = F.len;
+    if (F.len > 0 && lo >= 0) f0 = lbound(F.p, 0, f1, lo + 1, false);
+    if (F.len > 0 && hi != INT_MAX) f1 = lbound(F.p, f0, f1, hi, false);
+    const bool lx = (L.lo_mask >> l) & 1u, hx = (L.hi_mask >> l) & 1u;
+    // lane i: candidate x_i, its list V and the cuts of both lists
+    ListRef V{nullptr, 0, 0, nullptr, 0};
+    int a0 = f0, a1 = f0, v0 = 0, v1 = 0, nsV = 0, nsF = 0;
+    if (lane < nb && f0 < f1) {
+        const int32_t x = ld(cand, lane, cand_shared);
+        V = op_list(g, L.op_dir[iV], x);
+        const int32_t lo_i = lx ? max(lo, x) : lo, hi_i = hx ? min(hi, x) : hi;
+        nsV = (lo_i >= 0 ? 1 : 0) + (hi_i != INT_MAX ? 1 : 0);
+        nsF = (lx && x > lo ? 1 : 0) + (hx && x < hi ? 1 : 0);
+        v1 = V.len;
+        if (v1 > 0 && lo_i >= 0) v0 = lbound(V.p, 0, v1, lo_i + 1, false);
+        if (v0 < v1 && hi_i != INT_MAX) v1 = lbound(V.p, v0, v1, hi_i, false);
+        a1 = f1;
+        if (lx && x > lo) a0 = lbound(F.p, f0, f1, x + 1, false);
+        if (hx && x < hi) a1 = lbound(F.p, a0, f1, x, false);
+        if (v1 < v0) v1 = v0;
+        if (a1 < a0) a1 = a0;
+    }
+    const int na = a1 - a0, nv = v1 - v0;
+    const bool fdrv = na <= nv;                 // F's range drives, V is probed
+    const int run = (na == 0 || nv == 0) ? 0 : min(na, nv);
+    const int other = max(na, nv);
+    const bool merge = ra.merge_ratio > 0 && run >= MERGE_MIN_RUN && (long long)other <= (long long)ra.merge_ratio * run;
+    const uint32_t neq = L.neq_mask & below;    // x_i itself is never in its own list V(x_i)
+    if (MODE == MODE_STATS) {
+        // offsets of V (F's once), bound searches, the level's formula over the
+        // cut ranges, and the bytes each pair's strategy moves
+        unsigned long long b = 0, t = 0;
+        if (lane < nb && f0 < f1) {
+            b += 8 + nsV * search_bytes(V.len) + nsF * search_bytes(f1 - f0);
+            t += 32 + 32ull * (nsV * search_sectors(V.len) + nsF * search_sectors(f1 - f0));
+            if (run) {
+                const int plen = fdrv ? V.len : F.len;
+                b += 4ull * run + probe_bytes(other, run, plen);
+                if (merge) t += 4ull * (na + nv) + 64;
+                else t += 4ull * run + 32ull * run * ((fdrv ? V.T : F.T) ? 1ull : search_sectors(other));
+            }
+        }
+        b = warp_sum64(b);
+        t = warp_sum64(t);
+        if (lane == 0) {
+            const int nsF = (lo >= 0 ? 1 : 0) + (hi != INT_MAX ? 1 : 0);  // F's cut, once per batch
+            st.bytes += b + 8 + nsF * search_bytes(F.len);
+            st.touched += t + 32 + 32ull * nsF * search_sectors(F.len);
+        }
+        const unsigned long long e = warp_sum64(run);
+        if (lane == 0) st.leaf += e;
+    }
+    unsigned long long cnt = 0;
+    // long pairs of similar length: merged, the whole warp per pair
+    for (unsigned mm = __ballot_sync(FULL, merge); mm; mm &= mm - 1) {
+        const int i = __ffs(mm) - 1;
+        const int32_t* Vp = shfl_ptr(V.p, i);
+        const int b0 = __shfl_sync(FULL, v0, i), b1 = __shfl_sync(FULL, v1, i);
+        const int c0 = __shfl_sync(FULL, a0, i), c1 = __shfl_sync(FULL, a1, i);
+        if (c1 - c0 <= b1 - b0)
+            cnt += merge_count(F.p, c0, c1, Vp, b0, b1, ws.mtile, neq, ws.m, lane);
+        else
+            cnt += merge_count(Vp, b0, b1, F.p, c0, c1, ws.mtile, neq, ws.m, lane);
+    }
+    // the rest: one flattened space of driver ids
+    const int r = merge ? 0 : run;
+    int pend = r;  // inclusive prefix of r over the lanes
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, pend, o);
+        if (lane >= o) pend += y;
+    }
+    const int total = __shfl_sync(FULL, pend, 31);
+    if (total == 0) return cnt;
+    // driver ids of pair i: dptr[j], j = t - pre_i for flattened positions
+    // t in [pre_i, pend_i); the probe: a hash table of ptn > 0 slots at ptab,
+    // or -ptn ascending ids at ptab (binary search)
+    const int pre = pend - r;
+    const int32_t* dptr = fdrv ? F.p + a0 : V.p + v0;
+    const int32_t* ptab;
+    int ptn;
+    if (fdrv) {
+        ptab = V.T ? V.tab : V.p + v0;
+        ptn = V.T ? (int)V.T : -nv;
+    } else {
+        ptab = F.T ? F.tab : F.p + a0;
+        ptn = F.T ? (int)F.T : -na;
+    }
+    for (int t0 = 0; t0 < total; t0 += 128) {
+        int32_t x[4];
+        bool ok[4];
+        const int32_t* tb[4];
+        int tn[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int t = t0 + 32 * u + lane;
+            // pair of position t: the number of pairs whose range ends at or before t
+            int i = 0;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1)
+                if (__shfl_sync(FULL, pend, i + s - 1) <= t) i += s;
+            const int pi = __shfl_sync(FULL, pre, i);
+            const int32_t* di = shfl_ptr(dptr, i);
+            tb[u] = shfl_ptr(ptab, i);
+            tn[u] = __shfl_sync(FULL, ptn, i);
+            ok[u] = t < total;
+            x[u] = ok[u] ? __ldg(di + (t - pi)) : 0;
+        }
+        bool f[4], dn[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (!ok[u]) {
+                f[u] = false;
+                dn[u] = true;
+            } else if (tn[u] > 0) {
+                dn[u] = hash_first(tb[u], (uint32_t)tn[u], x[u], f[u]);
+            } else {
+                const int q = lbound(tb[u], 0, -tn[u], x[u], false);
+                f[u] = q < -tn[u] && __ldg(tb[u] + q) == x[u];
+                dn[u] = true;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (ok[u] && !dn[u]) f[u] = hash_has(tb[u], (uint32_t)tn[u], x[u]);
+            for (uint32_t nm = neq; nm && f[u]; nm &= nm - 1) f[u] = x[u] != ws.m[__ffs(nm) - 1];
+            cnt += f[u] ? 1 : 0;
+        }
+    }
+    return cnt;
 }
 
 // Adds a 128-bit value on lane 0 to the lane's running count, or straight to
@@ -696,15 +1111,15 @@ __device__ __forceinline__ void add_count(unsigned long long& acc, unsigned __in
 // sets pv[] under the partial match m_0..m_{l-1}, combined into the number
 // of tuples of pairwise distinct nodes (see XmPlanDev).
 template <int MODE>
-__device__ __noinline__ unsigned __int128 leaf_product(const XmPlanDev& P, const XmLevel* __restrict__ pv, const GraphDev& g,
-                                          WarpSmem& ws, int l, int lane, const RunArgs& ra,
-                                          unsigned long long& stat_bytes, unsigned long long& leaf_elems) {
+__device__ __noinline__ unsigned __int128 leaf_product(const XmPlanDev& P, const XmLevel* __restrict__ pv,
+                                                       const GraphDev& g, WarpSmem& ws, int l, int lane,
+                                                       const RunArgs& ra, Stats& st) {
     LvState& S = ws.st[l];
     auto size_of = [&](int i) -> unsigned long long {
         const XmLevel& V = pv[i];
-        stat_bytes += setup_lists<MODE>(V, g, ws, S, lane);
+        setup_lists<MODE>(V, g, ws, S, lane, st, false);
         unsigned long long c = 0;
-        if (!S.empty) c = leaf_tail<MODE>(P, V, g, ws, S, l, lane, ra, stat_bytes, leaf_elems, S.c0, S.c1);
+        if (!S.empty) c = leaf_tail<MODE>(P, V, g, ws, S, l, lane, ra, st, S.c0, S.c1);
         return __shfl_sync(FULL, c, 0);
     };
     typedef unsigned __int128 u128;
@@ -736,19 +1151,15 @@ __device__ __noinline__ unsigned __int128 leaf_product(const XmPlanDev& P, const
     return (u128)s1 * s2 * s4 - (u128)s3 * s4 - (u128)s5 * s2 - (u128)s6 * s1 + (u128)2 * s7;
 }
 
-struct Stats {
-    unsigned long long bytes = 0, ext = 0, sets = 0, units = 0, leaf = 0;
-};
-
 // Sets up level nl and builds its first window `win`; false when empty.
 template <int MODE>
 __device__ bool descend(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* win, int W, int nl, int lane,
                         const RunArgs& ra, Stats& st) {
-    st.bytes += setup_level<MODE>(P, g, ws, nl, lane);
+    setup_level<MODE>(P, g, ws, nl, lane, st, true);
     if (MODE == MODE_STATS && lane == 0) st.sets++;
     LvState& N = ws.st[nl];
     if (N.empty) return false;
-    scan_level<MODE, true>(P, P.lv[nl], g, ws, N, nl, win, W, lane, ra, st.bytes);
+    scan_level<MODE, true>(P, P.lv[nl], g, ws, N, nl, win, W, lane, ra, st);
     if (lane == 0) {
         N.complete = N.drv_pos >= N.drv_end;
         N.it_ptr = win;
@@ -767,11 +1178,14 @@ __device__ bool descend(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
 // iteration state is set; levels wl0.. use windows wins + (l - wl0) * W;
 // the last level is counted (or emitted) into acc. With PROD (counting with
 // a leaf product, sets ra.pv) the walk ends at level prod_p, which adds the
-// product (values past 64 bits go straight to the global counter).
+// product (values past 64 bits go straight to *counter).
 template <int MODE, bool PROD>
 __device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* wins, int W, int wl0, int lane,
-                        const RunArgs& ra, unsigned long long& acc, Stats& st, const Budget& budget, int l0 = 1) {
+                        const RunArgs& ra, unsigned long long& acc, unsigned long long* counter, Stats& st,
+                        const Budget& budget, int l0 = 1) {
     const int k = PROD ? P.prod_p + 1 : P.k;
+    // two-list last levels are counted a batch of candidates at a time
+    const int iF = (!PROD && MODE != MODE_EMIT) ? batch_leaf_fixed_op(P) : -1;
     int l = l0;
     unsigned steps = 0;
     while (l >= l0) {
@@ -781,8 +1195,20 @@ __device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
             if (S.complete || S.drv_pos >= S.drv_end) { l--; continue; }
             if (lane == 0) { S.wcnt = 0; S.wpos = 0; }
             __syncwarp();
-            scan_level<MODE, true>(P, P.lv[l], g, ws, S, l, wins + (size_t)(l - wl0) * W, W, lane, ra, st.bytes);
+            scan_level<MODE, true>(P, P.lv[l], g, ws, S, l, wins + (size_t)(l - wl0) * W, W, lane, ra, st);
             if (lane == 0) S.it_hi = S.wcnt;
+            __syncwarp();
+            continue;
+        }
+        if (iF >= 0 && l + 1 == k - 1) {
+            const int nb = min(32, S.it_hi - S.wpos);
+            acc += leaf_batch<MODE>(P, g, ws, iF, S.it_ptr + S.wpos, S.it_shared, nb, lane, ra, st);
+            if (MODE == MODE_STATS && lane == 0) {
+                st.ext += nb;
+                st.sets += nb;
+            }
+            __syncwarp();
+            if (lane == 0) S.wpos += nb;
             __syncwarp();
             continue;
         }
@@ -793,10 +1219,9 @@ __device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
         if (MODE == MODE_STATS && lane == 0) st.ext++;
         if (l + 1 == k - 1) {
             if (PROD)
-                add_count(acc, leaf_product<MODE>(P, ra.pv, g, ws, l + 1, lane, ra, st.bytes, st.leaf),
-                          ra.ctl + CTL_COUNT_LO, lane);
+                add_count(acc, leaf_product<MODE>(P, ra.pv, g, ws, l + 1, lane, ra, st), counter, lane);
             else
-                acc += leaf_level<MODE>(P, g, ws, l + 1, lane, ra, st.bytes, st.leaf);
+                acc += leaf_level<MODE>(P, g, ws, l + 1, lane, ra, st);
             if (MODE == MODE_STATS && lane == 0) st.sets++;
             continue;
         }
@@ -918,13 +1343,16 @@ __global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
 // the lists in registers instead of a level state in shared memory (the
 // general path's per-unit set-up dominated these kernels' shared-memory and
 // local-memory traffic). Chooses the driver and cut exactly as setup_level
-// and level2_cut do, so the pieces match the work units. Returns false
-// (nothing counted) when the level needs the general path: difference
-// lists, more than two probe lists, or a probe without a hash table.
-// Survivors are counted per lane into acc.
+// and level2_cut do, so the pieces match the work units. With one probe
+// list, the list is cut to the piece's ids and merged with the piece when
+// the cut is at most ra.merge_ratio times the piece (else hashed probes).
+// Returns false (nothing counted) when the level needs the general path:
+// difference lists, more than two probe lists, or a probe without a hash
+// table that is not merged. Survivors are counted per lane into acc.
+template <int MODE>
 __device__ __forceinline__ bool leaf3_direct(const XmPlanDev& P, const GraphDev& g, int32_t m0, int32_t m1,
                                              const int32_t* set, int set_len, int pos0, int per, int lane,
-                                             unsigned long long& acc) {
+                                             unsigned long long& acc, const RunArgs& ra, WarpSmem& ws, Stats& st) {
     const XmLevel& L = P.lv[2];
     if (L.ndiff) return false;
     ListRef mine{nullptr, 0, 0, nullptr, 0};
@@ -955,10 +1383,11 @@ __device__ __forceinline__ bool leaf3_direct(const XmPlanDev& P, const GraphDev&
         }
     }
     if (nlists > 3 || (use_reuse && dsrc != -1)) return false;  // > 2 probes, or the set as a probe
-    // probes: the operands other than the driver, each with a hash table
+    // probes: the operands other than the driver
     const int32_t* tab[2] = {nullptr, nullptr};
     uint32_t T[2] = {0, 0};
-    int np = 0;
+    int plen[2] = {0, 0};
+    int np = 0, psrc = -1;
     bool hashed = true;
     for (int i = 0; i < L.nops; i++) {
         if (i == dsrc || (use_reuse && ((L.reuse_ops >> i) & 1u))) continue;
@@ -969,37 +1398,90 @@ __device__ __forceinline__ bool leaf3_direct(const XmPlanDev& P, const GraphDev&
         if (np < 2) {
             tab[np] = ti;
             T[np] = Ti;
+            plen[np] = __shfl_sync(FULL, mine.len, i);
         }
+        if (np == 0) psrc = i;
         np++;
     }
-    if (!hashed) return false;
+    const bool try_merge = np == 1 && ra.merge_ratio > 0;
+    if (!hashed && !try_merge) return false;
     const int32_t* dp =
         dsrc == -1 ? set
                    : reinterpret_cast<const int32_t*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.p), dsrc));
+    if (MODE == MODE_STATS && lane == 0) {
+        st.bytes += 8ull * (nlists - (use_reuse ? 1 : 0));
+        st.touched += 32ull * (nlists - (use_reuse ? 1 : 0));
+    }
     if (empty) return true;
     const int32_t m[2] = {m0, m1};
     int32_t lo, hi;
     level_bounds(L, m, lo, hi);
     int c0 = 0, c1 = dlen;
-    if (lo >= 0) c0 = lbound(dp, 0, c1, lo + 1, false);
-    if (hi != INT_MAX) c1 = lbound(dp, c0, c1, hi, false);
+    if (lo >= 0) c0 = warp_lbound(dp, 0, c1, lo + 1, false, lane);
+    if (hi != INT_MAX) c1 = warp_lbound(dp, c0, c1, hi, false, lane);
+    if (MODE == MODE_STATS && lane == 0) {
+        const int ns = (lo >= 0 ? 1 : 0) + (hi != INT_MAX ? 1 : 0);
+        st.bytes += ns * search_bytes(dlen);
+        st.touched += 32ull * ns * search_sectors(dlen);
+    }
     const int pos = min(c1, c0 + pos0);
     const int end = min(c1, pos + per);
     if (pos >= end) return true;
     // matched nodes that may lie in the candidates (-1: none)
     const int32_t y0 = (L.neq_mask & 1u) ? m0 : -1;
     const int32_t y1 = (L.neq_mask & 2u) ? m1 : -1;
+    const long long run = end - pos;
+    if (MODE == MODE_STATS && lane == 0) st.leaf += run;
     if (np == 0) {
         if (lane == 0) {
-            long long c = end - pos;
+            long long c = run;
             for (int32_t y : {y0, y1}) {
                 if (y < 0) continue;
                 const int q = lbound(dp, pos, end, y, false);
                 if (q < end && __ldg(dp + q) == y) c--;
+                if (MODE == MODE_STATS) {
+                    st.bytes += search_bytes(end - pos);
+                    st.touched += 32ull * search_sectors(end - pos);
+                }
             }
             acc += c;
         }
         return true;
+    }
+    long long cut0 = -1;
+    if (np == 1) {
+        const int32_t* B = reinterpret_cast<const int32_t*>(
+            __shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.p), psrc));
+        const int blen = plen[0];
+        if (MODE == MODE_STATS) {
+            // accounting only: the probe list cut to the piece's ids
+            int pb, eb;
+            warp_lbound2(B, 0, blen, __ldg(dp + pos), 0, blen, __ldg(dp + end - 1) + 1, pb, eb, lane);
+            cut0 = eb - pb;
+        }
+        if (try_merge && run >= MERGE_MIN_RUN && (long long)blen <= (long long)ra.merge_ratio * run) {
+            // the whole probe list is within the ratio: merged whole, no cut
+            if (MODE == MODE_STATS && lane == 0) {
+                st.bytes += 4ull * run + probe_bytes(cut0, run, blen);
+                st.touched += 4ull * (run + blen) + 64;
+            }
+            if (lane == 0) {
+                ws.m[0] = m0;
+                ws.m[1] = m1;
+            }
+            __syncwarp();
+            acc += merge_count(dp, pos, end, B, 0, blen, ws.mtile, L.neq_mask & 3u, ws.m, lane);
+            return true;
+        }
+    }
+    if (!hashed) return false;
+    if (MODE == MODE_STATS && lane == 0) {
+        st.bytes += 4ull * run;
+        st.touched += 4ull * run;
+        for (int p = 0; p < np && p < 2; p++) {
+            st.bytes += probe_bytes(p == 0 && cut0 >= 0 ? cut0 : plen[p], run, plen[p]);
+            st.touched += 32ull * run;
+        }
     }
     unsigned cnt = 0;
     for (int base = pos; base < end; base += 128) {
@@ -1037,8 +1519,9 @@ __device__ __forceinline__ bool leaf3_direct(const XmPlanDev& P, const GraphDev&
 //      the first-level node when injectivity demands and it lies inside.
 // One lane per first-level candidate of the unit [a, b); returns the lane's
 // count.
+template <int MODE>
 __device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDev& g, int kind, int32_t m0,
-                                               const int32_t* set, int set_len, int a, int b, int lane) {
+                                               const int32_t* set, int set_len, int a, int b, int lane, Stats& st) {
     const XmLevel& L = P.lv[2];
     const int32_t lo0 = (L.lo_mask & 1u) ? m0 : -1;
     const int32_t hi0 = (L.hi_mask & 1u) ? m0 : INT_MAX;
@@ -1051,10 +1534,17 @@ __device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDe
     }
     const int c0 = lo0 >= 0 ? lbound(list, 0, len, lo0 + 1, false) : 0;
     const int c1 = hi0 != INT_MAX ? lbound(list, c0, len, hi0, false) : len;
-    unsigned long long acc = 0;
+    if (MODE == MODE_STATS && lane == 0) {
+        const int ns = (lo0 >= 0 ? 1 : 0) + (hi0 != INT_MAX ? 1 : 0);
+        st.bytes += (kind == 2 ? 8ull : 0ull) + ns * search_bytes(len);
+        st.touched += (kind == 2 ? 32ull : 0ull) + 32ull * ns * search_sectors(len);
+    }
+    const int per_cand = kind == 1 ? 0 : ((L.lo_mask & 2u) ? 1 : 0) + ((L.hi_mask & 2u) ? 1 : 0) + ((L.neq_mask & 2u) ? 1 : 0);
+    unsigned long long acc = 0, nc = 0;
     for (int i = a + lane; i < b; i += 32) {
         const int32_t m1 = __ldg(set + i);
         int lo = c0, hi = c1;
+        nc++;
         if (kind == 1) {
             // positions in the set are the candidates' own indices
             if (L.lo_mask & 2u) lo = max(lo, i + 1);
@@ -1074,13 +1564,25 @@ __device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDe
             acc += c;
         }
     }
+    if (MODE == MODE_STATS && per_cand) {
+        // every candidate's bound searches over the cut list
+        const unsigned long long s = warp_sum((unsigned)nc);
+        if (lane == 0) {
+            st.bytes += s * per_cand * search_bytes(c1 - c0);
+            st.touched += 32ull * s * per_cand * search_sectors(c1 - c0);
+        }
+    }
     return acc;
 }
 
-// ROOTS (count mode, no product): the count of every unit goes to the
-// 128-bit counter of its start node, ra.root_counts[2 v .. 2 v + 1].
-template <int MODE, bool PROD, bool ROOTS = false>
-__global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+// With ra.root_counts (count mode) the count of every unit goes to the
+// 128-bit counter of its start-node index i (the position in the root list,
+// or the node id without one), ra.root_counts[2 i .. 2 i + 1]. (A run-time
+// switch: a third template flag for it made ptxas fail on the product
+// kernel.)
+template <int MODE, bool PROD>
+__global__ void __launch_bounds__(512, 2) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+    const bool ROOTS = MODE == MODE_COUNT && ra.root_counts != nullptr;
     extern __shared__ __align__(16) unsigned char smem[];
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(smem);
     plan_to_smem(P, plan_g);
@@ -1092,10 +1594,12 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
     constexpr bool prod = PROD;
     const int ke = prod ? P.prod_p + 1 : k;
     const int W = ra.window;
-    const size_t warp_bytes = warp_state_bytes(k) + (size_t)n_windows(k) * W * sizeof(int32_t);
+    const size_t warp_bytes = match_warp_bytes(k, W);
     unsigned char* wbase = smem + plan_bytes(k) + (size_t)wib * warp_bytes;
     WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase);
     int32_t* wins = reinterpret_cast<int32_t*>(wbase + warp_state_bytes(k));  // level l >= 2 at (l-2)*W
+    if (lane == 0) ws.mtile = wins + (size_t)n_windows(k) * W;
+    __syncwarp();
     const GraphDev& g = ra.g;
     const bool two_level = !ra.l2_units;
     // unit index space: pieces of a start node's first-level set, or pieces
@@ -1112,6 +1616,8 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
     budget.start(ra.ctl, ra.budget_ns, lane);
     int owner = -1;
     int acc_root = -1;  // ROOTS: start-node index the running count belongs to
+    unsigned long long* counter = ra.ctl + CTL_COUNT_LO;
+    if (MODE == MODE_STATS && lane == 0) atomicCAS(ra.ctl + CTL_W_START, 0ull, global_ns());
     for (;;) {
         long long start;
         int cnt;
@@ -1135,9 +1641,10 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
             if (ROOTS) {
                 const int rt = two_level ? owner : __ldg(ra.l1root + owner);
                 if (rt != acc_root) {
-                    if (acc_root >= 0) flush_count(acc, ra.root_counts + 2 * (size_t)root_node(ra, acc_root), lane);
+                    if (acc_root >= 0) flush_count(acc, counter, lane);
                     acc = 0;
                     acc_root = rt;
+                    counter = ra.root_counts + 2 * (size_t)rt;
                 }
             }
             if (MODE == MODE_STATS && lane == 0) st.units++;
@@ -1148,9 +1655,13 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                 const int32_t* base = ra.l1set + s0;
                 const int a = chunk * ra.unit;
                 const int b = min(s1 - s0, a + ra.unit);
-                if (MODE == MODE_STATS && lane == 0) st.bytes += 4ull * (b - a);
-                if (MODE == MODE_COUNT && ra.leaf_kind) {
-                    acc += leaf_closed_form(P, g, ra.leaf_kind, root_node(ra, root), base, s1 - s0, a, b, lane);
+                if (MODE == MODE_STATS && lane == 0) {
+                    st.bytes += 4ull * (b - a);
+                    st.touched += 4ull * (b - a);
+                }
+                if (MODE != MODE_EMIT && ra.leaf_kind) {
+                    acc += leaf_closed_form<MODE>(P, g, ra.leaf_kind, root_node(ra, root), base, s1 - s0, a, b, lane,
+                                                  st);
                     continue;
                 }
                 if (lane == 0) {
@@ -1167,7 +1678,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                     S1.drv_pos = S1.drv_end = 0;
                 }
                 __syncwarp();
-                if (!explore<MODE, PROD>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget, 1)) stop = true;
+                if (!explore<MODE, PROD>(P, g, ws, wins, W, 2, lane, ra, acc, counter, st, budget, 1)) stop = true;
                 continue;
             }
             if (two_level) {
@@ -1178,7 +1689,6 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                 const int a = chunk * ra.unit;
                 const int b = min(s1 - s0, a + ra.unit);
                 const int32_t rnode = root_node(ra, root);
-                if (MODE == MODE_STATS && lane == 0) st.bytes += 4ull * (b - a);
                 if (MODE == MODE_EMIT) {
                     for (int p = a; p < b; p += 32) {
                         const bool ok = p + lane < b;
@@ -1200,9 +1710,13 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
             const int e = owner;
             const int root = __ldg(ra.l1root + e);
             const int s0 = set_start(ra, root), s1 = set_start(ra, root + 1);
-            if (MODE == MODE_COUNT && ke == 3 &&
-                leaf3_direct(P, g, root_node(ra, root), __ldg(ra.l1set + e), ra.l1set + s0, s1 - s0, chunk * per2,
-                             per2, lane, acc))
+            if (MODE == MODE_STATS && lane == 0) {
+                st.bytes += 4;
+                st.touched += 4;
+            }
+            if (MODE != MODE_EMIT && ke == 3 &&
+                leaf3_direct<MODE>(P, g, root_node(ra, root), __ldg(ra.l1set + e), ra.l1set + s0, s1 - s0,
+                                   chunk * per2, per2, lane, acc, ra, ws, st))
                 continue;
             if (lane == 0) {
                 ws.m[0] = root_node(ra, root);
@@ -1218,17 +1732,18 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
             __syncwarp();
             if (MODE == MODE_STATS && lane == 0) st.ext++;
             if (ke == 3) {
-                acc += leaf_level<MODE>(P, g, ws, 2, lane, ra, st.bytes, st.leaf, chunk * per2, per2);
+                acc += leaf_level<MODE>(P, g, ws, 2, lane, ra, st, chunk * per2, per2);
                 if (MODE == MODE_STATS && lane == 0) st.sets++;
                 continue;
             }
-            st.bytes += setup_level<MODE>(P, g, ws, 2, lane);
+            setup_level<MODE>(P, g, ws, 2, lane, st, false);
             if (MODE == MODE_STATS && lane == 0) st.sets++;
             LvState& S2 = ws.st[2];
             if (S2.empty) continue;
             const int pos = min(S2.c1, S2.c0 + chunk * per2);
             const int end = min(S2.c1, pos + per2);
             if (pos >= end) continue;
+            account_scan<MODE>(S2, end - pos, st, lane);
             const bool whole = pos == S2.c0 && end == S2.c1;
             if (lane == 0) {
                 S2.drv_pos = pos;
@@ -1236,7 +1751,7 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
             }
             __syncwarp();
             int32_t* win = wins;  // level 2's window
-            scan_level<MODE, true>(P, P.lv[2], g, ws, S2, 2, win, W, lane, ra, st.bytes);
+            scan_level<MODE, true>(P, P.lv[2], g, ws, S2, 2, win, W, lane, ra, st);
             if (lane == 0) {
                 S2.complete = whole && S2.drv_pos >= S2.drv_end;
                 S2.it_ptr = win;
@@ -1248,21 +1763,25 @@ __global__ void __launch_bounds__(512, 3) k_match(const XmPlanDev* __restrict__ 
                 S2.set_shared = 1;
             }
             __syncwarp();
-            if (!explore<MODE, PROD>(P, g, ws, wins, W, 2, lane, ra, acc, st, budget, 2)) stop = true;
+            if (!explore<MODE, PROD>(P, g, ws, wins, W, 2, lane, ra, acc, counter, st, budget, 2)) stop = true;
         }
         if (stop) break;
     }
-    if (ROOTS) {
-        if (acc_root >= 0) flush_count(acc, ra.root_counts + 2 * (size_t)root_node(ra, acc_root), lane);
-    } else {
-        flush_count(acc, ra.ctl + CTL_COUNT_LO, lane);
-    }
+    if (!ROOTS || acc_root >= 0) flush_count(acc, counter, lane);
     if (MODE == MODE_STATS && lane == 0) {
         atomicAdd(ra.ctl + CTL_STATS + 0, st.bytes);
         atomicAdd(ra.ctl + CTL_STATS + 1, st.ext);
         atomicAdd(ra.ctl + CTL_STATS + 2, st.sets);
         atomicAdd(ra.ctl + CTL_STATS + 3, st.units);
         atomicAdd(ra.ctl + CTL_STATS + 4, st.leaf);
+        atomicAdd(ra.ctl + CTL_STATS + 6, st.touched);
+        // load balance of the persistent grid: when each warp ran out of work
+        const unsigned long long t = global_ns();
+        const unsigned long long t0 = *((volatile unsigned long long*)(ra.ctl + CTL_W_START));
+        atomicMax(ra.ctl + CTL_W_FIRST, ~t);
+        atomicMax(ra.ctl + CTL_W_LAST, t);
+        atomicAdd(ra.ctl + CTL_W_SUM, t - t0);
+        atomicAdd(ra.ctl + CTL_W_COUNT, 1ull);
     }
 }
 
@@ -1281,10 +1800,13 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(wbase);
     WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase + plan_bytes(b.kmax));
     int32_t* wins = reinterpret_cast<int32_t*>(wbase + plan_bytes(b.kmax) + warp_state_bytes(b.kmax));
+    if (lane == 0) ws.mtile = wins + (size_t)(b.kmax > 2 ? b.kmax - 2 : 0) * W;
+    __syncwarp();
     const long long total = __ldg(b.unit_prefix + b.npairs);
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     RunArgs ra{};  // count mode: no emission buffer
     ra.window = W;
+    ra.merge_ratio = b.merge_ratio;
     GraphDev g{};
     Stats st;
     Budget budget;
@@ -1327,11 +1849,12 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
                 if (lane == 0) ws.m[0] = v;
                 __syncwarp();
                 if (k == 2) {
-                    acc += leaf_level<MODE_COUNT>(P, g, ws, 1, lane, ra, st.bytes, st.leaf);
+                    acc += leaf_level<MODE_COUNT>(P, g, ws, 1, lane, ra, st);
                     continue;
                 }
                 if (!descend<MODE_COUNT>(P, g, ws, wins, W, 1, lane, ra, st)) continue;
-                if (!explore<MODE_COUNT, false>(P, g, ws, wins, W, 1, lane, ra, acc, st, budget)) {
+                if (!explore<MODE_COUNT, false>(P, g, ws, wins, W, 1, lane, ra, acc, b.counts + 2 * (size_t)cur, st,
+                                                budget)) {
                     stop = true;
                     break;
                 }
@@ -1479,10 +2002,7 @@ cudaError_t scan_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_
 
 size_t batch_warp_bytes(int kmax, int window) { return batch_warp_bytes_impl(kmax, window); }
 
-size_t match_smem_bytes(int k, int window, int warps) {
-    size_t warp_bytes = warp_state_bytes(k) + (size_t)n_windows(k) * window * sizeof(int32_t);
-    return plan_bytes(k) + warp_bytes * warps;
-}
+size_t match_smem_bytes(int k, int window, int warps) { return plan_bytes(k) + match_warp_bytes(k, window) * warps; }
 
 int64_t chunk_capacity(int32_t n, int64_t m) { return (int64_t)n + (m + L1_CHUNK - 1) / L1_CHUNK; }
 
@@ -1580,12 +2100,11 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
     const size_t smem = match_smem_bytes(P.k, b.window, warps_per_block);
     const bool prod = b.pv != nullptr;
     const bool roots = b.root_counts != nullptr;
-    if (roots && (mode != MODE_COUNT || prod)) return cudaErrorInvalidValue;
-    const void* fn = mode == MODE_STATS ? (prod ? (const void*)k_match<MODE_STATS, true>
-                                                : (const void*)k_match<MODE_STATS, false>)
+    if (roots && mode != MODE_COUNT) return cudaErrorInvalidValue;
+    const void* fn = mode == MODE_STATS  ? (prod ? (const void*)k_match<MODE_STATS, true>
+                                                 : (const void*)k_match<MODE_STATS, false>)
                      : mode == MODE_EMIT ? (const void*)k_match<MODE_EMIT, false>
                      : prod              ? (const void*)k_match<MODE_COUNT, true>
-                     : roots             ? (const void*)k_match<MODE_COUNT, false, true>
                                          : (const void*)k_match<MODE_COUNT, false>;
     if ((err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return err;
@@ -1604,8 +2123,6 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
         k_match<MODE_EMIT, false><<<grid, block, smem, stream>>>(plan_dev, b);
     else if (prod)
         k_match<MODE_COUNT, true><<<grid, block, smem, stream>>>(plan_dev, b);
-    else if (roots)
-        k_match<MODE_COUNT, false, true><<<grid, block, smem, stream>>>(plan_dev, b);
     else
         k_match<MODE_COUNT, false><<<grid, block, smem, stream>>>(plan_dev, b);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;

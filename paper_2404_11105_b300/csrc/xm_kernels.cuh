@@ -53,6 +53,15 @@ inline uint32_t hash_table_size(int64_t len) {
     return t;
 }
 
+// Ids per tile of the merge intersection: 32 lanes x one 16-byte load.
+constexpr int MERGE_TILE = 128;
+// Default list-length ratio below which two lists are merged instead of
+// probing the longer one once per id of the shorter (RunArgs::merge_ratio).
+constexpr int MERGE_RATIO_DEFAULT = 8;
+// Shorter lists than this are never merged: one round of probes costs less
+// than the merge's per-tile rounds.
+constexpr int MERGE_MIN_RUN = 64;
+
 // Builds the hash tables of one CSR side on `stream` (tables pre-filled with -1).
 cudaError_t build_hash_index(const int32_t* off, const int32_t* adj, const int64_t* hoff, int32_t* htab, int32_t n,
                              cudaStream_t stream);
@@ -66,8 +75,14 @@ enum {
     CTL_STATUS = 4,    // error bits (1: unit count overflow, 2: time budget exceeded)
     CTL_T0 = 5,        // global-timer start of the matcher (budget reference)
     CTL_L1_HEAD = 6,   // next first-level chunk (count pass); 7: write pass
-    CTL_STATS = 8,     // 8 stats words (xm_stats order)
-    CTL_WORDS = 16
+    CTL_STATS = 8,     // 8 stats words: algorithmic bytes, extensions, set operations, units, leaf
+                       // elements (matcher); first-level bytes; touched bytes (matcher); unused
+    CTL_W_START = 16,  // instrumented matcher: global timer when the first warp started,
+    CTL_W_FIRST = 17,  // ~(earliest warp exit), latest warp exit, sum of warp exits after the
+    CTL_W_LAST = 18,   // start, warps
+    CTL_W_SUM = 19,
+    CTL_W_COUNT = 20,
+    CTL_WORDS = 24
 };
 
 struct RunArgs {
@@ -97,6 +112,9 @@ struct RunArgs {
                                                 // (2 words per node id), else null
     const XmLevel* pv = nullptr;  // leaf-product sets of the device plan when counting
                                   // with a product (set by launch_match), else null
+    int32_t merge_ratio = MERGE_RATIO_DEFAULT;  // count-mode leaves with two lists: merge both when
+                                                // the longer (cut to the shorter's id range) is at
+                                                // most this many times the shorter; <= 0: never
 };
 
 enum { MODE_COUNT = 0, MODE_STATS = 1, MODE_EMIT = 2 };
@@ -115,6 +133,7 @@ struct BatchDev {
     int32_t window;                  // candidate window per level (ids)
     unsigned long long budget_ns;    // time budget (0: none)
     int32_t kmax;                    // largest pattern in the batch
+    int32_t merge_ratio;             // as RunArgs::merge_ratio
 };
 
 // Shared memory per warp of the batched matcher.

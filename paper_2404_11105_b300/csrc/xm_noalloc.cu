@@ -88,6 +88,24 @@ extern "C" int xm_count_noalloc(const int32_t* out_off, const int32_t* out_adj, 
     int rc = scratch_for_current_device(&base);
     if (rc) return rc;
     cudaStream_t stream = (cudaStream_t)stream_;
+    {
+        // the kernels size their scans and first-level arrays from m: both
+        // CSRs must end at m, or they would read past the lists and the
+        // scratch pieces (two 4-byte reads into host memory, no allocation)
+        int32_t ends[2] = {-1, -1};
+        cudaError_t e = cudaMemcpyAsync(&ends[0], out_off + n, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], in_off + n, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            set_error(std::string("xm_count_noalloc: reading the CSR ends: ") + cudaGetErrorString(e));
+            return XM_ECUDA;
+        }
+        if (ends[0] != m || ends[1] != m) {
+            set_error("xm_count_noalloc: out_off[n] and in_off[n] must both equal m (got " + std::to_string(ends[0]) +
+                      ", " + std::to_string(ends[1]) + ", m = " + std::to_string(m) + ")");
+            return XM_EINVAL;
+        }
+    }
     unsigned char* q = base;
     RunArgs a;
     a.g = {out_off, out_adj, in_off, in_adj, n};
@@ -114,6 +132,7 @@ extern "C" int xm_count_noalloc(const int32_t* out_off, const int32_t* out_adj, 
     a.out = nullptr;
     a.capacity = 0;
     a.budget_ns = (unsigned long long)p->tuning.budget_ms * 1000000ull;
+    a.merge_ratio = p->tuning.merge_ratio;
     // the control block (work counter, count accumulators, status) must
     // start at zero; every other array is fully written before it is read
     cudaError_t e = cudaMemsetAsync(a.ctl, 0, CTL_WORDS * sizeof(unsigned long long), stream);

@@ -147,7 +147,7 @@ int xm_server_submit(xm_server s, xm_plan p, int32_t graph_index, int64_t tag, i
     for (Slot& c : s->slots)
         if (!c.busy) { sl = &c; break; }
     if (!sl || s->in_flight + L.total > s->budget) return XM_OK;  // not now: no slot or memory
-    e = cudaMallocAsync(&sl->scratch, L.total, sl->stream);
+    e = dev_alloc_async(&sl->scratch, L.total, sl->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return XM_OK;  // the pool could not serve it now: retry later
@@ -177,6 +177,7 @@ int xm_server_submit(xm_server s, xm_plan p, int32_t graph_index, int64_t tag, i
     a.unit = p->tuning.unit;
     a.window = p->tuning.window;
     a.budget_ns = (unsigned long long)p->tuning.budget_ms * 1000000ull;
+    a.merge_ratio = p->tuning.merge_ratio;
     memcpy(sl->host + kHostPlan, &p->plan.dev, sizeof(XmPlanDev));
     e = cudaMemsetAsync(a.ctl, 0, CTL_WORDS * sizeof(unsigned long long), sl->stream);
     if (e == cudaSuccess)
@@ -187,7 +188,7 @@ int xm_server_submit(xm_server s, xm_plan p, int32_t graph_index, int64_t tag, i
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sl->host + kHostCtl, a.ctl, CTL_WORDS * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, sl->stream);
-    if (e == cudaSuccess) e = cudaFreeAsync(sl->scratch, sl->stream);
+    if (e == cudaSuccess) e = dev_free_async(sl->scratch, sl->stream);
     if (e == cudaSuccess) e = cudaEventRecord(sl->done, sl->stream);
     if (e != cudaSuccess) return fail(e, "query launch");
     sl->busy = true;

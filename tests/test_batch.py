@@ -53,9 +53,11 @@ def test_batch_tunings_graph_replay_and_autotuner(xm, setup):
     b.run(graph=True)
     assert b.counts() == ref
     best, ms = b.tune([(128, 16, 4, 0, 0), (256, 64, 8, 0, 0), (64, 4, 8, 2, 0)], reps=2)
-    assert ms > 0 and best in ({"window": 128, "unit": 16, "warps_per_block": 4, "blocks_per_sm": 0, "budget_ms": 0},
-                               {"window": 256, "unit": 64, "warps_per_block": 8, "blocks_per_sm": 0, "budget_ms": 0},
-                               {"window": 64, "unit": 4, "warps_per_block": 8, "blocks_per_sm": 2, "budget_ms": 0})
+    launch = {k: best[k] for k in ("window", "unit", "warps_per_block", "blocks_per_sm", "budget_ms")}
+    assert ms > 0 and best["merge_ratio"] == 8 and launch in (
+        {"window": 128, "unit": 16, "warps_per_block": 4, "blocks_per_sm": 0, "budget_ms": 0},
+        {"window": 256, "unit": 64, "warps_per_block": 8, "blocks_per_sm": 0, "budget_ms": 0},
+        {"window": 64, "unit": 4, "warps_per_block": 8, "blocks_per_sm": 2, "budget_ms": 0})
     b.run()
     assert b.counts() == ref
     b.free()

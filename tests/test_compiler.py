@@ -115,9 +115,17 @@ def test_shared_endpoints_are_reduced():
 def test_tuning_roundtrip_and_validation():
     p = xm.Plan(synth.BIFAN)
     p.set_tuning(window=256, unit=16, warps_per_block=4, blocks_per_sm=2)
-    assert p.tuning() == {"window": 256, "unit": 16, "warps_per_block": 4, "blocks_per_sm": 2, "budget_ms": 0}
-    with pytest.raises(xm.XmError):
-        p.set_tuning(window=100)
+    # merge_ratio 0 resolves to the default length ratio (8)
+    assert p.tuning() == {"window": 256, "unit": 16, "warps_per_block": 4, "blocks_per_sm": 2, "budget_ms": 0,
+                          "merge_ratio": 8}
+    p.set_tuning(merge_ratio=-1)
+    assert p.tuning()["merge_ratio"] == -1
+    p.set_tuning(merge_ratio=1024)
+    assert p.tuning()["merge_ratio"] == 1024
+    for bad in (dict(window=100), dict(merge_ratio=-2), dict(merge_ratio=1025)):
+        with pytest.raises(xm.XmError):
+            p.set_tuning(**bad)
+    assert p.tuning()["merge_ratio"] == 1024
 
 
 DENSE = [synth.random_pattern(k, 0.9, 123, k) for k in (6, 7, 8)] + \

@@ -320,3 +320,89 @@ def test_motif_census_identities():
     plain = np.array([g.count_matches(synth.MOTIFS3[nm]) for nm in names], dtype=object)
     assert sum(induced) == connected_triples
     assert list(C.dot(induced)) == list(plain)
+
+
+# ------------------------------------------- rooted enumeration, triangles --
+
+@pytest.mark.parametrize("pattern", [synth.BIFAN, synth.CYCLE4, synth.BIPARALLEL, synth.FFL,
+                                     (4, [(0, 1), (1, 2), (2, 0), (2, 3)])])
+def test_enumerate_embeddings_vs_brute_force(pattern):
+    """Every embedding with the root vertex's node in a range, against all
+    node k-tuples."""
+    n, src, dst = random_small_graph(8, 0.45, 31)
+    arcs = simple_arcs(n, src, dst)
+    k, parcs = pattern
+    g = oracle.OracleGraph(n, src, dst)
+    for root, lo, hi in ((0, 0, n), (1, 2, 5), (k - 1, 6, 7), (0, 3, 3)):
+        want = sorted(t for t in itertools.product(range(n), repeat=k)
+                      if len(set(t)) == k and lo <= t[root] < hi and all((t[u], t[v]) in arcs for u, v in parcs))
+        got = g.enumerate_embeddings(pattern, root, lo, hi)
+        assert [tuple(r) for r in got.tolist()] == want
+        assert g.count_embeddings(pattern, root, lo, hi) == len(want)
+
+
+def test_triangle_sums_vs_brute_force_and_matrices():
+    """Feed-forward triangles and closed 3-walks per source range against
+    brute force over node triples (tiny graphs) and sparse matrix products
+    (R-MAT scale 10); additive over a partition of the sources."""
+    for seed in (0, 1):
+        n, src, dst = random_small_graph(9, 0.4, 40 + seed)
+        arcs = simple_arcs(n, src, dst)
+        ffl = sum(1 for a, b, c in itertools.permutations(range(n), 3)
+                  if (a, b) in arcs and (b, c) in arcs and (a, c) in arcs)
+        walks = sum(1 for a, b, c in itertools.permutations(range(n), 3)
+                    if (a, b) in arcs and (b, c) in arcs and (c, a) in arcs)
+        g = oracle.OracleGraph(n, src, dst)
+        assert g.triangle_sums() == (ffl, walks)
+    n, src, dst = synth.rmat_graph(10, 6, seed=17)
+    A = adjacency(n, src, dst)
+    A2 = A @ A
+    g = oracle.OracleGraph(n, src, dst)
+    f, c = g.triangle_sums()
+    assert f == int(A.multiply(A2).sum())
+    assert c == int((A2 @ A).diagonal().sum())
+    assert f == g.count_matches(synth.FFL) and c == 3 * g.count_matches(synth.CYCLE3)
+    cuts = [0, 1, 7, 300, n]
+    parts = [g.triangle_sums(a, b) for a, b in zip(cuts, cuts[1:])]
+    assert (sum(p[0] for p in parts), sum(p[1] for p in parts)) == (f, c)
+
+
+@pytest.mark.parametrize("pattern", [synth.BIFAN, synth.CYCLE4, synth.BIPARALLEL, synth.FFCHAIN5,
+                                     synth.MOTIFS3["300"], synth.MOTIFS3["201"]])
+def test_canonicalize_restores_orbit_minimum(pattern):
+    """Each orbit-smallest row, moved by a random automorphism (a different
+    embedding of the same match whenever the automorphism moves a vertex),
+    is mapped back to the row itself."""
+    n, src, dst = random_small_graph(9, 0.7, 5)
+    g = oracle.OracleGraph(n, src, dst)
+    rows = g.enumerate(pattern)
+    assert rows.shape[0] > 0
+    aut = oracle.automorphisms(pattern)
+    rng = np.random.default_rng(9)
+    pick = aut[rng.integers(0, aut.shape[0], rows.shape[0])]
+    moved = np.take_along_axis(rows, pick, axis=1)        # moved[i][v] = rows[i][s(v)]
+    if aut.shape[0] > 1:
+        assert not np.array_equal(moved, rows)
+    assert np.array_equal(oracle.canonicalize(pattern, moved), rows)
+    # every embedding of the match canonicalises to the same row
+    for s in aut:
+        assert np.array_equal(oracle.canonicalize(pattern, rows[:, s]), rows)
+
+
+def test_capped_walk_counts_or_gives_up():
+    """The capped walk returns the exact rooted count whenever it finishes
+    within its candidate budget, gives up (None) below the work the walk
+    needs, and finishes for every root once the cap is large."""
+    n, src, dst = synth.rmat_graph(9, 8, seed=17)
+    g = oracle.OracleGraph(n, src, dst)
+    for pat in (synth.BIFAN, synth.CYCLE4, synth.FFCHAIN5):
+        gave_up = 0
+        for v in range(0, n, 17):
+            want = g.count_embeddings(pat, 0, v, v + 1)
+            assert g.count_embeddings_capped(pat, 0, v, v + 1, 1 << 40) == want
+            got = g.count_embeddings_capped(pat, 0, v, v + 1, 50)
+            assert got is None or got == want
+            gave_up += got is None
+        assert gave_up > 0
+    # cap 1: only walks that examine at most one candidate finish
+    assert g.count_embeddings_capped(synth.BIFAN, 0, 0, 1, 1) is None

@@ -24,8 +24,12 @@ def graph_pair(xm, n, src, dst):
     return xm.Graph(n, src, dst), oracle.OracleGraph(n, src, dst)
 
 
-TUNINGS = [dict(), dict(window=64, unit=1, warps_per_block=2), dict(window=96, unit=7, warps_per_block=4),
-           dict(window=128, unit=3, warps_per_block=1, blocks_per_sm=1)]
+# launch shapes, and the three intersection strategies of two-list last
+# levels: the default length-ratio choice, merging whenever possible
+# (merge_ratio 1024) and never merging (probes only)
+TUNINGS = [dict(), dict(window=64, unit=1, warps_per_block=2, merge_ratio=1024),
+           dict(window=96, unit=7, warps_per_block=4, merge_ratio=-1),
+           dict(window=128, unit=3, warps_per_block=1, blocks_per_sm=1, merge_ratio=1)]
 
 NAMED = {"cycle3": synth.CYCLE3, "ffl": synth.FFL, "bifan": synth.BIFAN, "cycle4": synth.CYCLE4,
          "biparallel": synth.BIPARALLEL, "ffchain5": synth.FFCHAIN5}
@@ -152,6 +156,32 @@ def test_root_range_additivity(xm, rmat_small):
             assert xm.xm_count_range(g, pe, r, r + 1) == og.count_embeddings(pat, pe.start, r, r + 1)
 
 
+def test_count_roots_each(xm, rmat_small):
+    """Per-start-node counts in one launch: each equals the oracle rooted at
+    the plan's start vertex (embeddings mode) and the one-node range count
+    (matches); repeated and unsorted nodes keep the caller's order; the
+    per-node counts add up to xm_count_roots; leaf-product plans too."""
+    g, og = rmat_small
+    rng = np.random.default_rng(8)
+    roots = np.concatenate([rng.integers(0, g.n, 40), [0, 1, 2, 0, 7, g.n - 1]]).astype(np.int32)
+    for pat in (synth.BIFAN, synth.CYCLE4, synth.BIPARALLEL, synth.FFCHAIN5, synth.FFL,
+                PRODUCT_PATTERNS["path4"], (2, [(0, 1)])):
+        pe = xm.Plan(pat, xm.XM_EMBEDDINGS | xm.XM_NO_SPLIT)
+        for tun in (TUNINGS[0], TUNINGS[1], TUNINGS[2]):
+            pe.set_tuning(**tun)
+            got = xm.xm_count_roots_each(g, pe, roots)
+            want = [og.count_embeddings(pat, pe.start, v, v + 1) for v in roots.tolist()]
+            assert got == want, (pat, tun)
+        p = xm.Plan(pat)
+        per = xm.xm_count_roots_each(g, p, roots)
+        assert per == [xm.xm_count_range(g, p, v, v + 1) for v in roots.tolist()]
+        uniq = np.unique(roots)
+        assert sum(xm.xm_count_roots_each(g, p, uniq)) == xm.xm_count_roots(g, p, uniq)
+    assert xm.xm_count_roots_each(g, xm.Plan(synth.BIFAN), np.zeros(0, np.int32)) == []
+    with pytest.raises(xm.XmError):
+        xm.xm_count_roots_each(g, xm.Plan(synth.BIFAN), np.array([-1], np.int32))
+
+
 def test_enumerate_sets_rmat_small(xm, rmat_small):
     g, og = rmat_small
     for pat in (synth.FFL, synth.CYCLE4, synth.FFCHAIN5):
@@ -228,11 +258,59 @@ def s20(xm):
     return g, og
 
 
+def test_s20_triangles_closed_forms(xm, s20):
+    """The two triangle motifs on the whole scale-20 graph against the
+    oracle's closed forms (tests/golden/rmat20_triangles.json, written by
+    make_rmat20_triangles.py from the oracle alone): feed-forward triangles
+    sum(A o A^2) and directed 3-cycles tr(A^3)/3, under every intersection
+    strategy (length-ratio choice, always merge, never merge)."""
+    import json
+    import os
+    g, og = s20
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rmat20_triangles.json")))
+    for name, key in (("030T", "030T_feed_forward_triangles"), ("030C", "030C_directed_3_cycles")):
+        for ratio in (0, 1024, -1):
+            p = xm.Plan(synth.MOTIFS3[name])
+            p.set_tuning(merge_ratio=ratio)
+            assert xm.xm_count(g, p) == gold[key], (name, ratio)
+
+
+def s20_roots(og, hubs=12, uniform=48, seed=20):
+    """Start nodes for per-node checks on the scale-20 graph: the nodes of
+    highest degree whose rooted walks the oracle still finishes in about a
+    second (total degree at most 6000: the top hubs, of degree up to ~50,000,
+    would take the single-threaded oracle minutes per motif) and seeded
+    uniform nodes."""
+    off, adj = og.out_csr()
+    outdeg = np.diff(off)
+    indeg = np.bincount(adj, minlength=og.n)
+    deg = outdeg + indeg
+    heavy = np.nonzero(deg <= 6000)[0]
+    heavy = heavy[np.argsort(-deg[heavy], kind="stable")][:hubs]
+    rng = np.random.default_rng(seed)
+    return np.concatenate([heavy, rng.integers(0, og.n, uniform)]).astype(np.int32), deg
+
+
+def test_s20_motifs_per_root_with_hubs(xm, s20):
+    """All 13 motifs at full size: per-start-node embedding counts (one launch
+    per motif through xm_count_roots_each) against the oracle rooted at the
+    plan's start vertex, on hub nodes of degree 1500-6000 -- whose work is
+    split into many 1024-id pieces -- and uniform nodes."""
+    g, og = s20
+    roots, deg = s20_roots(og)
+    assert (deg[roots[:12]] > 1500).all()
+    for name, pat in synth.MOTIFS3.items():
+        pe = xm.Plan(pat, xm.XM_EMBEDDINGS)
+        got = xm.xm_count_roots_each(g, pe, roots)
+        for v, c in zip(roots.tolist(), got):
+            assert c == og.count_embeddings(pat, pe.start, v, v + 1), (name, v)
+
+
 def test_s20_motifs_sampled_and_closed_forms(xm, s20):
     """All 13 motifs at full size in the bench's launch configuration:
-    closed forms where they are cheap (stars, 2-path), and per-start-node
-    embedding counts against the oracle on sampled start nodes (hubs and
-    uniform), plus reduced == unreduced on the whole graph."""
+    closed forms where they are cheap (stars, 2-path), reduced == unreduced
+    on the whole graph, one-node ranges == per-node counts (hub nodes 0-3
+    included)."""
     g, og = s20
     off, adj = og.out_csr()
     outdeg = np.diff(off)
@@ -247,19 +325,13 @@ def test_s20_motifs_sampled_and_closed_forms(xm, s20):
     assert xm.xm_count(g, xm.Plan(synth.MOTIFS3["021D"])) == int(c2(outdeg.astype(object)))
     assert xm.xm_count(g, xm.Plan(synth.MOTIFS3["021U"])) == int(c2(indeg.astype(object)))
     assert xm.xm_count(g, xm.Plan(synth.MOTIFS3["021C"])) == int((indeg.astype(object) * outdeg - r).sum())
-    rng = np.random.default_rng(20)
-    # heavy start nodes the single-threaded oracle still finishes quickly
-    deg = outdeg + indeg
-    heavy = np.nonzero(deg <= 1500)[0]
-    heavy = heavy[np.argsort(-deg[heavy])][:8]
-    roots = np.concatenate([heavy, rng.integers(0, og.n, 24)])
     for name, pat in synth.MOTIFS3.items():
         red = xm.xm_count(g, xm.Plan(pat))
         assert red == xm.xm_count(g, xm.Plan(pat, xm.XM_NO_REDUCE)), name
+        # per start node, through the one-node range entry point
         pe = xm.Plan(pat, xm.XM_EMBEDDINGS)
-        for v in roots:
-            v = int(v)
-            assert xm.xm_count_range(g, pe, v, v + 1) == og.count_embeddings(pat, pe.start, v, v + 1), (name, v)
+        for v in (0, 1, 2, 3, 12345, og.n - 1):
+            assert xm.xm_count_range(g, pe, v, v + 1) == xm.xm_count_roots_each(g, pe, [v])[0], (name, v)
 
 
 DENSE = [synth.random_pattern(k, 0.9, 123, k) for k in (6, 7, 8)] + \
@@ -361,9 +433,16 @@ def test_plan_autotuner(xm, rmat_small):
     want = og.count_matches(synth.BIFAN)
     cands = [(64, 1, 2, 0, 0), (256, 8, 8, 0, 0), (512, 32, 4, 1, 0)]
     best, ms = xm.xm_plan_tune(g, p, cands, reps=2)
-    assert ms > 0 and tuple(best.values()) in cands
+    assert ms > 0 and tuple(best.values())[:5] in cands and best["merge_ratio"] == 8
     assert p.tuning() == best
     assert xm.xm_count(g, p) == want
+    # on a start-node list, with the intersection strategy as a knob
+    roots = np.arange(0, g.n, 3, dtype=np.int32)
+    want_roots = xm.xm_count_roots(g, p, roots)
+    cands = [(64, 1, 2, 0, 0, -1), (256, 8, 8, 0, 0, 8), (512, 32, 4, 1, 0, 1024)]
+    best, ms = xm.xm_plan_tune(g, p, cands, reps=2, roots=roots)
+    assert ms > 0 and tuple(best.values()) in cands
+    assert xm.xm_count_roots(g, p, roots) == want_roots
 
 
 # ------------------------------------------------ leaf products (Sec. 5.3)

@@ -54,3 +54,37 @@ def test_noalloc_rejects_graphs_beyond_its_scratch(xm):
         _noalloc(xm, g, xm.Plan(synth.FFL))
     assert ei.value.status == xm.XM_EINVAL
     assert "too large" in str(ei.value)
+
+
+def test_noalloc_near_its_limit_with_hub_lists(xm):
+    """A skewed graph whose scratch nearly fills the fixed area: hub lists of
+    hundreds of ids take the paths that differ between the two entry points
+    (xm_count probes hash tables and counts three-vertex levels from
+    registers; the allocation-free call has no hash tables and falls back to
+    merges and binary searches)."""
+    n, src, dst = synth.rmat_graph(17, 16, seed=41)
+    g = xm.Graph(n, src, dst)
+    need = 4 * (3 * g.n + 3.001 * g.m)
+    assert 0.6 * (32 << 20) < need < (32 << 20)
+    oo, oa, io, ia = g.csr_pointers()
+    for pat in (synth.CYCLE3, synth.FFL, synth.MOTIFS3["030T"], synth.BIPARALLEL,
+                (4, [(0, 1), (1, 2), (2, 3)])):
+        p = xm.Plan(pat)
+        want = xm.xm_count(g, p)
+        assert want > 0
+        assert xm.xm_count_noalloc(oo, oa, io, ia, g.n, g.m, p) == want
+        assert xm.xm_count_noalloc(oo, oa, io, ia, g.n, g.m, p) == want
+
+
+def test_noalloc_rejects_inconsistent_arc_counts(xm):
+    """m must equal out_off[n] and in_off[n]: a wrong m is refused before
+    any kernel runs, and the next correct call still works."""
+    n, src, dst = synth.er_graph(300, 2500, seed=4)
+    g = xm.Graph(n, src, dst)
+    oo, oa, io, ia = g.csr_pointers()
+    p = xm.Plan(synth.BIFAN)
+    for bad_m in (g.m + 1, g.m - 1, 0):
+        with pytest.raises(xm.XmError) as ei:
+            xm.xm_count_noalloc(oo, oa, io, ia, g.n, bad_m, p)
+        assert ei.value.status == xm.XM_EINVAL
+    assert xm.xm_count_noalloc(oo, oa, io, ia, g.n, g.m, p) == xm.xm_count(g, p)
