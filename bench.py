@@ -160,17 +160,43 @@ def start_node_sample(n, one_in):
 
 # ------------------------------------------------------- sharding (N > 1) --
 
+def root_costs(n, src, dst):
+    """Estimated work of the walk from each start node: deg(v) times the
+    summed degrees of v's neighbours (a walk extends v by each neighbour and
+    each of those by its own list), plus one; total (out + in) degrees of the
+    input arcs. On power-law graphs this grows much faster than deg(v)."""
+    deg = np.bincount(src, minlength=n).astype(np.float64) + np.bincount(dst, minlength=n)
+    nb = np.bincount(src, weights=deg[dst], minlength=n) + np.bincount(dst, weights=deg[src], minlength=n)
+    return deg * nb + deg + 1.0
+
+
+def balanced_cuts(cost, world):
+    """Cut points 0 = c_0 <= ... <= c_world = len(cost) of contiguous pieces
+    of about equal total cost."""
+    cum = np.cumsum(cost)
+    cuts = [0] + [int(np.searchsorted(cum, cum[-1] * r / world)) for r in range(1, world)] + [len(cost)]
+    for r in range(1, len(cuts)):
+        cuts[r] = min(max(cuts[r], cuts[r - 1]), len(cost))
+    return cuts
+
+
 def shard_bounds(n, src, dst, world):
-    """Contiguous start-node ranges, one per rank, balanced by arc count
-    (out + in degree); together they cover [0, n) exactly once."""
+    """Contiguous start-node ranges, one per rank, balanced by the estimated
+    walk cost of their start nodes (root_costs); together they cover [0, n)
+    exactly once."""
     if world <= 1:
         return [(0, n)]
-    deg = np.bincount(src, minlength=n).astype(np.int64) + np.bincount(dst, minlength=n)
-    cum = np.cumsum(deg)
-    cuts = [0] + [int(np.searchsorted(cum, cum[-1] * r / world)) for r in range(1, world)] + [n]
-    for r in range(1, len(cuts)):
-        cuts[r] = max(cuts[r], cuts[r - 1])
+    cuts = balanced_cuts(root_costs(n, src, dst), world)
     return [(cuts[r], cuts[r + 1]) for r in range(world)]
+
+
+def shard_roots(roots, cost, world, rank):
+    """Rank `rank`'s contiguous piece of the sorted start-node sample,
+    balanced by the estimated cost of its start nodes."""
+    if world <= 1:
+        return roots
+    cuts = balanced_cuts(cost[roots], world)
+    return roots[cuts[rank]: cuts[rank + 1]]
 
 
 def allreduce_counts(counts, dist, device="cpu"):
@@ -411,10 +437,13 @@ def run_batch(args):
             out.append(e0.elapsed_time(e1))
         return out
 
+    budget = args.batch_pair_budget_ms
     batch = xm.Batch(plans, graphs, pairs)
+    batch.set_pair_budget(budget)
     # autotuner on a sub-batch of pairs (every 16th pair), then applied to all
     sub = xm.Batch(plans, graphs, pairs[::16])
-    cands = [(w, u, wpb, 0, 0) for w in (128, 256) for u in (16, 64, 256) for wpb in (4, 8)]
+    sub.set_pair_budget(budget)
+    cands = [(w, u, wpb, 0, 0, mr) for w in (128, 256) for u in (16, 64, 256) for wpb in (4, 8) for mr in (-1, 2)]
     best, best_ms = sub.tune(cands, reps=2)
     sub.free()
     batch.set_tuning(**best)
@@ -431,24 +460,32 @@ def run_batch(args):
     with ClockSampler(0) as clk:
         ms_batch = timed(one_launch, args.steps)
     clocks = clk.summary()
-    # one launch per pattern (same kernel, P launches)
+    status = batch.pair_status()
+    ok = status == xm.XM_OK
+    # one launch per pattern (same kernel, P launches, same budgets)
     per_pattern = [xm.Batch([plans[pi]], graphs, [(0, gi) for gi in range(G)]) for pi in range(P)]
     for b in per_pattern:
         b.set_tuning(**best)
-    pp_counts = []
+        b.set_pair_budget(budget)
+    pp_counts, pp_ok = [], []
 
     def pattern_launches():
         pp_counts.clear()
+        pp_ok.clear()
         for b in per_pattern:
             b.run()
         for b in per_pattern:
             pp_counts.extend(b.counts())
+            pp_ok.extend((b.pair_status() == xm.XM_OK).tolist())
 
     ms_pp = timed(pattern_launches, max(1, args.steps // 2))
-    assert pp_counts == counts, "per-pattern launches disagree with the single batched launch"
-    # one xm_count call per pair on a seeded sample, extrapolated
+    both = [i for i in range(npairs) if ok[i] and pp_ok[i]]
+    assert all(pp_counts[i] == counts[i] for i in both), "per-pattern launches disagree with the batched launch"
+    # one xm_count call per pair on a seeded sample of the pairs that finished
+    # within their budget, extrapolated to all pairs
     rng = np.random.default_rng(7)
-    sample = rng.choice(npairs, size=min(args.batch_single_sample, npairs), replace=False)
+    done = np.nonzero(ok)[0]
+    sample = rng.choice(done, size=min(args.batch_single_sample, len(done)), replace=False)
 
     def singles():
         for i in sample:
@@ -459,20 +496,24 @@ def run_batch(args):
     ms_single_sample = timed(singles, 1)[0]
     ms_single = ms_single_sample * npairs / len(sample)
     ms = statistics.median(ms_batch)
-    total = sum(counts)
+    total = sum(c for c, k in zip(counts, ok) if k)
     line = {"metric": "patterns/s", "value": npairs / (ms / 1000.0), "unit": "(pattern, graph) pairs/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"{P} random connected patterns (k 3-{args.batch_kmax}, density 0.3-0.7, seed 4) "
                                    f"x {G} small graphs (n log-uniform 50-{args.batch_nmax}, mean out-degree 4-12, "
                                    f"ER/R-MAT alternating, seed 5)", "pairs": npairs, "matches_per_step": total,
+                       "pair_budget_ms": budget, "pairs_within_budget": int(ok.sum()),
+                       "pairs_over_budget": int((~ok).sum()),
                        "graph_load_s": round(load_s, 1), "autotuned": best,
                        "autotune_sub_batch_ms": round(best_ms, 3)},
             "matches_per_s": total / (ms / 1000.0),
             "vs_one_launch_per_pattern": {"ms": statistics.median(ms_pp),
                                           "speedup": statistics.median(ms_pp) / ms},
             "vs_one_call_per_pair": {"ms_extrapolated": ms_single, "sample_pairs": int(len(sample)),
-                                     "speedup": ms_single / ms},
+                                     "speedup": ms_single / ms,
+                                     "how": "one xm_count per pair on a seeded sample of the pairs within budget, "
+                                            "scaled to all pairs"},
             "gpu_launches": args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
@@ -486,7 +527,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="xm", choices=["xm", "reference"])
-    ap.add_argument("--workload", default="rmat20",
+    ap.add_argument("--workload", default="rmat24",
                     choices=["rmat20", "tiny", "rmat22", "rmat24", "dense", "batch", "serve"])
     ap.add_argument("--serve-graphs", type=int, default=1000)
     ap.add_argument("--serve-rates", default="100,300,1000,3000,10000")
@@ -500,6 +541,8 @@ def main():
     ap.add_argument("--batch-nmax", type=int, default=5000, help="largest graph (nodes) in the batch")
     ap.add_argument("--batch-single-sample", type=int, default=400,
                     help="pairs timed one xm_count call at a time (extrapolated)")
+    ap.add_argument("--batch-pair-budget-ms", type=int, default=20,
+                    help="device-time budget of each (pattern, graph) pair (0: none)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
@@ -508,8 +551,8 @@ def main():
                     help="also time the oracle in this many concurrent processes (-1: all host cores, at most 64)")
     ap.add_argument("--no-stats", action="store_true", help="skip the instrumented run (roofline bytes)")
     ap.add_argument("--patterns", default="", help="comma-separated subset of the workload's patterns")
-    ap.add_argument("--root-sample", type=int, default=1024,
-                    help="rmat24: count over a seeded uniform sample of 1/N of the start nodes")
+    ap.add_argument("--root-sample", type=int, default=4096,
+                    help="rmat22/rmat24: count over a seeded uniform sample of 1/N of the start nodes")
     ap.add_argument("--budget-ms", type=int, default=0, help="device-time budget per count call (0: none)")
     ap.add_argument("--merge-ratio", type=int, default=0,
                     help="intersection strategy threshold of two-list last levels (0: library default, -1: "
@@ -557,7 +600,8 @@ def main():
     roots = None
     if args.workload in ("rmat22", "rmat24"):
         roots, sample_desc = start_node_sample(n, args.root_sample)
-        roots = roots[(roots >= r_lo) & (roots < r_hi)]
+        if world > 1:
+            roots = shard_roots(roots, root_costs(n, src, dst), world, rank)
         desc += "; " + sample_desc
 
     def count_one(p):
@@ -581,8 +625,9 @@ def main():
         # project autotuner (untimed, part of warm-up): window, unit size,
         # warps per block and the intersection strategy's length ratio, per
         # pattern on this graph (on the start-node sample when there is one)
-        cands = [(w, u, wpb, 0, args.budget_ms, mr) for w in (256, 512) for wpb in (4, 8) for u in (8, 32)
-                 for mr in ((args.merge_ratio,) if args.merge_ratio else (-1, 8))]
+        windows = (256,) if roots is not None else (256, 512)
+        cands = [(w, u, wpb, 0, args.budget_ms, mr) for w in windows for wpb in (4, 8) for u in (8, 32)
+                 for mr in ((args.merge_ratio,) if args.merge_ratio else (-1, 2))]
         for name, p in plans.items():
             best, _ = xm.xm_plan_tune(g, p, cands, reps=1, roots=roots)
             tuned[name] = {k: best[k] for k in ("window", "unit", "warps_per_block", "merge_ratio")}

@@ -556,6 +556,22 @@ int xm_batch_counts(xm_batch b, uint64_t *out_counts, void *stream);
 int xm_batch_tune(xm_batch b, const xm_tuning *cand, int32_t ncand, int32_t reps, xm_tuning *best, float *best_ms,
                   void *stream);
 
+/*
+ * xm_batch_set_pair_budget -- a device-time budget for every pair of the
+ * batch (0 = none; the default). A pair whose work has run this long since
+ * its first work unit started (GPU global timer) stops: its remaining units
+ * are skipped and xm_batch_pair_status reports XM_ETIMEOUT for it; its count
+ * is incomplete. The other pairs finish exactly, and xm_batch_counts still
+ * returns XM_OK. The tuning's budget_ms, which ends the whole launch, stays
+ * separate. Drops a captured CUDA graph (captured again on the next
+ * xm_batch_run_graph).
+ *
+ * xm_batch_pair_status -- after a run: status[i] = XM_OK or XM_ETIMEOUT for
+ * pair i (host array of npairs int32). Synchronises `stream`.
+ */
+int xm_batch_set_pair_budget(xm_batch b, int32_t budget_ms);
+int xm_batch_pair_status(xm_batch b, int32_t *status, void *stream);
+
 /* Frees a batch. NULL is a no-op. */
 void xm_batch_free(xm_batch b);
 

@@ -33,7 +33,7 @@ EXPORTS = ["xm_strerror", "xm_last_error", "xm_version", "xm_load_graph", "xm_gr
            "xm_server_free", "xm_count_roots", "xm_enumerate_roots", "xm_count_roots_stats", "xm_plan_tune",
            "xm_plan_product", "xm_plan_product_set", "xm_plan_split", "xm_plan_split_part",
            "xm_plan_split_quotient", "xm_count_roots_each", "xm_plan_tune_roots", "xm_fault_inject",
-           "xm_device_bytes_live"]
+           "xm_device_bytes_live", "xm_batch_set_pair_budget", "xm_batch_pair_status"]
 
 
 class XmError(RuntimeError):
@@ -108,6 +108,8 @@ def _load():
         "xm_batch_tune": (ctypes.c_int, [vp, ctypes.POINTER(xm_tuning), i32, i32, ctypes.POINTER(xm_tuning),
                                          ctypes.POINTER(ctypes.c_float), vp]),
         "xm_batch_free": (None, [vp]),
+        "xm_batch_set_pair_budget": (ctypes.c_int, [vp, i32]),
+        "xm_batch_pair_status": (ctypes.c_int, [vp, i32p, vp]),
         "xm_count_batch": (ctypes.c_int, [i32, ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64, i32p, u64p, vp]),
         "xm_query_bytes": (ctypes.c_uint64, [vp, vp]),
         "xm_count_roots": (ctypes.c_int, [vp, vp, i32p, i64, u64p, u64p, vp]),
@@ -186,6 +188,21 @@ class Graph:
         ps = [ctypes.c_void_p() for _ in range(4)]
         _check(lib().xm_graph_csr(self._h, *[ctypes.byref(p) for p in ps]))
         return [p.value for p in ps]
+
+    def csr_host(self):
+        """Copies of the device CSR as numpy int32 arrays (out_off, out_adj,
+        in_off, in_adj); torch moves the bytes."""
+        import torch
+
+        class _View:  # a device array by pointer, for torch.as_tensor
+            def __init__(self, ptr, count):
+                self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<i4", "data": (ptr, True),
+                                                 "version": 3}
+
+        oo, oa, io, ia = self.csr_pointers()
+        sizes = (self.n + 1, self.m, self.n + 1, self.m)
+        return [torch.as_tensor(_View(p, c), device="cuda").cpu().numpy() if c else np.zeros(0, np.int32)
+                for p, c in zip((oo, oa, io, ia), sizes)]
 
     def last_timing(self):
         """(prep_ms, match_ms) of the last call, from CUDA events on its stream."""
@@ -392,6 +409,17 @@ class Batch:
         _check(lib().xm_batch_counts(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _stream(stream)))
         lo, hi = out[0::2], out[1::2]
         return [(int(h) << 64) | int(l) for l, h in zip(lo, hi)]
+
+    def set_pair_budget(self, budget_ms: int):
+        """Per-pair device-time budget (0: none); see pair_status()."""
+        _check(lib().xm_batch_set_pair_budget(self._h, int(budget_ms)))
+
+    def pair_status(self, stream=None):
+        """XM_OK or XM_ETIMEOUT per pair, after a run."""
+        st = np.zeros(self.npairs, np.int32)
+        _check(lib().xm_batch_pair_status(self._h, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          _stream(stream)))
+        return st
 
     def tune(self, candidates, reps=2, stream=None):
         arr = (xm_tuning * len(candidates))(*[xm_tuning(*c) for c in candidates])

@@ -372,98 +372,140 @@ int xm_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, 
     if (!out) { set_error("NULL output handle"); return XM_EINVAL; }
     if (flags != 0) { set_error("flags must be 0"); return XM_EINVAL; }
     if (n < 1 || m < 0) { set_error("n must be >= 1 and m >= 0"); return XM_EINVAL; }
+    if (m > 0 && (!src || !dst)) { set_error("NULL arc arrays"); return XM_EINVAL; }
+    if (m >= (int64_t)INT32_MAX) { set_error("fewer than 2^31 input arcs are supported"); return XM_EINVAL; }
     cudaStream_t stream = (cudaStream_t)stream_;
-    // host arrays of the build, kept between loads like the build's own
-    // staging (fresh pages cost a fault each on first touch); loads take turns
-    static std::mutex load_mu;
-    static HostVec<int32_t> hs, hd;
-    static HostCsr H;
-    std::lock_guard<std::mutex> load_lock(load_mu);
-    const int32_t* s = src;
-    const int32_t* d = dst;
-    try {
-        if (m > 0 && (is_device_ptr(src) || is_device_ptr(dst))) {
-            hs.resize(m);
-            hd.resize(m);
-            XM_CUDA(cudaMemcpyAsync(hs.data(), src, m * sizeof(int32_t), cudaMemcpyDefault, stream), "arc copy");
-            XM_CUDA(cudaMemcpyAsync(hd.data(), dst, m * sizeof(int32_t), cudaMemcpyDefault, stream), "arc copy");
-            XM_CUDA(cudaStreamSynchronize(stream), "arc copy");
-            s = hs.data();
-            d = hd.data();
+    xm_graph_s* g = new (std::nothrow) xm_graph_s();
+    if (!g) { set_error("host allocation failed"); return XM_ENOMEM; }
+    g->n = n;
+    // temporaries of the build, released before returning
+    int32_t *d_src = nullptr, *d_dst = nullptr, *ints = nullptr;
+    unsigned long long *k0 = nullptr, *k1 = nullptr;
+    auto release = [&]() {
+        cudaStreamSynchronize(stream);
+        dev_free(d_src);
+        dev_free(d_dst);
+        dev_free(ints);
+        dev_free(k0);
+        dev_free(k1);
+    };
+    auto fail = [&](cudaError_t e, const char* what) {
+        cudaGetLastError();
+        release();
+        free_graph(g);
+        set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA;
+    };
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) return fail(e, "cudaGetDevice");
+    // host arcs are uploaded; arc ids are checked on the device as the
+    // keys are packed
+    const bool on_device = m > 0 && is_device_ptr(src) && is_device_ptr(dst);
+    // scan partials and the control block first: the build's scans use them
+    const int64_t cmax_in = chunk_capacity(n, m);
+    const int64_t iscratch = csr_int_scratch(m, n);
+    g->n_block_sums = (std::max<int64_t>(std::max<int64_t>((int64_t)n + 1, cmax_in + 1), std::max(m + 2, iscratch)) +
+                       SCAN_TILE - 1) /
+                      SCAN_TILE;
+    if ((e = dev_alloc(&g->d_block_sums, g->n_block_sums * sizeof(int64_t))) != cudaSuccess)
+        return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_ctl, ctl_bytes())) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = cudaMemsetAsync(g->d_ctl, 0, ctl_bytes(), stream)) != cudaSuccess) return fail(e, "memset");
+    RunArgs sa{};
+    sa.block_sums = g->d_block_sums;
+    sa.n_block_sums = g->n_block_sums;
+    sa.ctl = g->d_ctl;
+    if ((e = dev_alloc(&ints, (size_t)iscratch * sizeof(int32_t))) != cudaSuccess) return fail(e, "device allocation");
+    unsigned long long* keys = nullptr;
+    int64_t mm = 0;
+    if (m > 0) {
+        const int32_t *s = src, *d = dst;
+        if (!on_device) {
+            if ((e = dev_alloc(&d_src, (size_t)m * sizeof(int32_t))) != cudaSuccess) return fail(e, "device allocation");
+            if ((e = dev_alloc(&d_dst, (size_t)m * sizeof(int32_t))) != cudaSuccess) return fail(e, "device allocation");
+            if ((e = cudaMemcpyAsync(d_src, src, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, stream)) != cudaSuccess)
+                return fail(e, "arc upload");
+            if ((e = cudaMemcpyAsync(d_dst, dst, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, stream)) != cudaSuccess)
+                return fail(e, "arc upload");
+            s = d_src;
+            d = d_dst;
         }
-        std::string err;
-        int rc = build_host_csr(n, m, s, d, H, err);
-        if (rc) { set_error(err); return rc; }
-        if ((int64_t)n + H.m >= (int64_t)INT32_MAX) { set_error("n + arcs must stay below 2^31"); return XM_EINVAL; }
-        xm_graph_s* g = new xm_graph_s();
-        g->n = n;
-        g->m = H.m;
-        XM_CUDA(cudaGetDevice(&g->device), "cudaGetDevice");
-        const size_t off_b = ((size_t)n + 1) * sizeof(int32_t);
-        const size_t adj_b = (size_t)std::max<int64_t>(H.m, 1) * sizeof(int32_t);
-        g->cmax = chunk_capacity(n, H.m);
-        if (g->cmax >= INT32_MAX) { delete g; set_error("graph too large for the chunk index"); return XM_EINVAL; }
-        g->n_block_sums = (std::max<int64_t>(std::max<int64_t>((int64_t)n + 1, g->cmax + 1), H.m + 2) + SCAN_TILE - 1) /
-                          SCAN_TILE;
-        cudaError_t e = cudaSuccess;
-        if (e == cudaSuccess) e = dev_alloc(&g->d_out_off, off_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_in_off, off_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_out_adj, adj_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_in_adj, adj_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_root_chunks, off_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_chunk_cnt, (size_t)(g->cmax + 1) * sizeof(int32_t));
-        if (e == cudaSuccess) e = dev_alloc(&g->d_l1set, adj_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_units, off_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_l1root, adj_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_e_units, adj_b + sizeof(int32_t));
-        if (e == cudaSuccess) e = dev_alloc(&g->d_block_sums, g->n_block_sums * sizeof(int64_t));
-        if (e == cudaSuccess) e = dev_alloc(&g->d_ctl, ctl_bytes());
-        for (auto& ev : g->ev)
-            if (e == cudaSuccess) e = cudaEventCreate(&ev);
-        if (e != cudaSuccess) {
+        if ((e = dev_alloc(&k0, (size_t)m * sizeof(unsigned long long))) != cudaSuccess)
+            return fail(e, "device allocation");
+        if ((e = dev_alloc(&k1, (size_t)m * sizeof(unsigned long long))) != cudaSuccess)
+            return fail(e, "device allocation");
+        if ((e = csr_sort_unique(n, m, s, d, k0, k1, ints, sa, &keys, &mm, stream)) != cudaSuccess)
+            return fail(e, "CSR sort");
+        unsigned long long status = 0;
+        if ((e = cudaMemcpy(&status, g->d_ctl + CTL_STATUS, sizeof status, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return fail(e, "status readback");
+        if (status & STATUS_BAD_ID) {
+            release();
             free_graph(g);
-            cudaGetLastError();
-            set_error(std::string("device allocation: ") + cudaGetErrorString(e));
-            return e == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA;
+            set_error("arc endpoint outside [0, n)");
+            return XM_EINVAL;
         }
-        const size_t am = (size_t)H.m * sizeof(int32_t);
-        e = cudaMemcpyAsync(g->d_out_off, H.out_off.data(), off_b, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_in_off, H.in_off.data(), off_b, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess && am) e = cudaMemcpyAsync(g->d_out_adj, H.out_adj.data(), am, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess && am) e = cudaMemcpyAsync(g->d_in_adj, H.in_adj.data(), am, cudaMemcpyHostToDevice, stream);
-        // hash index: per-list table offsets on the host, tables built on the device
-        std::vector<int64_t> hoff_out(n + 1, 0), hoff_in(n + 1, 0);
-        for (int32_t v = 0; v < n; v++) {
-            hoff_out[v + 1] = hoff_out[v] + hash_table_size(H.out_off[v + 1] - H.out_off[v]);
-            hoff_in[v + 1] = hoff_in[v] + hash_table_size(H.in_off[v + 1] - H.in_off[v]);
-        }
-        g->hash_slots = hoff_out[n] + hoff_in[n];
-        const size_t hoff_b = ((size_t)n + 1) * sizeof(int64_t);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_out_hoff, hoff_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_in_hoff, hoff_b);
-        if (e == cudaSuccess) e = dev_alloc(&g->d_out_htab, (size_t)std::max<int64_t>(hoff_out[n], 1) * sizeof(int32_t));
-        if (e == cudaSuccess) e = dev_alloc(&g->d_in_htab, (size_t)std::max<int64_t>(hoff_in[n], 1) * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_out_hoff, hoff_out.data(), hoff_b, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_in_hoff, hoff_in.data(), hoff_b, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess && hoff_out[n])
-            e = cudaMemsetAsync(g->d_out_htab, 0xFF, (size_t)hoff_out[n] * sizeof(int32_t), stream);
-        if (e == cudaSuccess && hoff_in[n])
-            e = cudaMemsetAsync(g->d_in_htab, 0xFF, (size_t)hoff_in[n] * sizeof(int32_t), stream);
-        if (e == cudaSuccess) e = build_hash_index(g->d_out_off, g->d_out_adj, g->d_out_hoff, g->d_out_htab, n, stream);
-        if (e == cudaSuccess) e = build_hash_index(g->d_in_off, g->d_in_adj, g->d_in_hoff, g->d_in_htab, n, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) {
-            free_graph(g);
-            cudaGetLastError();
-            set_error(std::string("graph upload / index build: ") + cudaGetErrorString(e));
-            return e == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA;
-        }
-        *out = g;
-        return XM_OK;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return XM_ENOMEM;
     }
+    if ((int64_t)n + mm >= (int64_t)INT32_MAX) {
+        release();
+        free_graph(g);
+        set_error("n + arcs must stay below 2^31");
+        return XM_EINVAL;
+    }
+    g->m = mm;
+    const size_t off_b = ((size_t)n + 1) * sizeof(int32_t);
+    const size_t adj_b = (size_t)std::max<int64_t>(mm, 1) * sizeof(int32_t);
+    g->cmax = chunk_capacity(n, mm);
+    if ((e = dev_alloc(&g->d_out_off, off_b)) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_in_off, off_b)) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_out_adj, adj_b)) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_in_adj, adj_b)) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = csr_emit(n, keys, keys == k0 ? k1 : k0, mm, ints, sa, g->d_out_off, g->d_out_adj, g->d_in_off,
+                      g->d_in_adj, stream)) != cudaSuccess)
+        return fail(e, "CSR emit");
+    // scratch of the matching pipeline
+    if ((e = dev_alloc(&g->d_root_chunks, off_b)) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_chunk_cnt, (size_t)(g->cmax + 1) * sizeof(int32_t))) != cudaSuccess)
+        return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_l1set, adj_b)) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_units, off_b)) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_l1root, adj_b)) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_e_units, adj_b + sizeof(int32_t))) != cudaSuccess) return fail(e, "device allocation");
+    for (auto& ev : g->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e, "cudaEventCreate");
+    // hash index: per-node table offsets (device scan), then the tables
+    const size_t hoff_b = ((size_t)n + 1) * sizeof(int64_t);
+    if ((e = dev_alloc(&g->d_out_hoff, hoff_b)) != cudaSuccess) return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_in_hoff, hoff_b)) != cudaSuccess) return fail(e, "device allocation");
+    int64_t slots[2] = {0, 0};
+    if ((e = hash_offsets(g->d_out_off, n, ints, sa, g->d_out_hoff, stream)) != cudaSuccess)
+        return fail(e, "hash offsets");
+    if ((e = cudaMemcpyAsync(&slots[0], g->d_out_hoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream)) !=
+        cudaSuccess)
+        return fail(e, "hash offsets");
+    if ((e = hash_offsets(g->d_in_off, n, ints, sa, g->d_in_hoff, stream)) != cudaSuccess)
+        return fail(e, "hash offsets");
+    if ((e = cudaMemcpyAsync(&slots[1], g->d_in_hoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream)) !=
+        cudaSuccess)
+        return fail(e, "hash offsets");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return fail(e, "graph build");
+    g->hash_slots = slots[0] + slots[1];
+    if ((e = dev_alloc(&g->d_out_htab, (size_t)std::max<int64_t>(slots[0], 1) * sizeof(int32_t))) != cudaSuccess)
+        return fail(e, "device allocation");
+    if ((e = dev_alloc(&g->d_in_htab, (size_t)std::max<int64_t>(slots[1], 1) * sizeof(int32_t))) != cudaSuccess)
+        return fail(e, "device allocation");
+    if (slots[0] && (e = cudaMemsetAsync(g->d_out_htab, 0xFF, (size_t)slots[0] * sizeof(int32_t), stream)) != cudaSuccess)
+        return fail(e, "memset");
+    if (slots[1] && (e = cudaMemsetAsync(g->d_in_htab, 0xFF, (size_t)slots[1] * sizeof(int32_t), stream)) != cudaSuccess)
+        return fail(e, "memset");
+    if ((e = build_hash_index(g->d_out_off, g->d_out_adj, g->d_out_hoff, g->d_out_htab, n, stream)) != cudaSuccess)
+        return fail(e, "hash index");
+    if ((e = build_hash_index(g->d_in_off, g->d_in_adj, g->d_in_hoff, g->d_in_htab, n, stream)) != cudaSuccess)
+        return fail(e, "hash index");
+    release();
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "graph build");
+    *out = g;
+    return XM_OK;
 }
 
 int xm_graph_info(xm_graph g, int32_t* n, int64_t* m) {
@@ -744,7 +786,15 @@ static int stage_roots(xm_graph g, const int32_t* roots, int64_t nroots, int64_t
         if (v < 0 || v >= g->n) { set_error("root id outside [0, n)"); return XM_EINVAL; }
     std::sort(r.begin(), r.end());
     r.erase(std::unique(r.begin(), r.end()), r.end());
-    if (!g->d_roots) XM_CUDA(dev_alloc(&g->d_roots, (size_t)g->n * sizeof(int32_t)), "root buffer");
+    if (!g->d_roots) {
+        cudaError_t e = dev_alloc(&g->d_roots, (size_t)g->n * sizeof(int32_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g->d_roots = nullptr;
+            set_error(std::string("root buffer: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA;
+        }
+    }
     if (!r.empty())
         XM_CUDA(cudaMemcpyAsync(g->d_roots, r.data(), r.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream),
                 "root upload");

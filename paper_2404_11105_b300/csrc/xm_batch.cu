@@ -24,6 +24,8 @@ struct xm_batch_s {
     long long* d_prefix = nullptr;
     unsigned long long* d_counts = nullptr;
     unsigned long long* d_ctl = nullptr;
+    unsigned long long* d_pair_words = nullptr;  // per pair: start time, status (per-pair budgets)
+    int32_t pair_budget_ms = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -54,6 +56,7 @@ void free_batch(xm_batch_s* b) {
     dev_free(b->d_prefix);
     dev_free(b->d_counts);
     dev_free(b->d_ctl);
+    dev_free(b->d_pair_words);
     delete b;
 }
 
@@ -80,12 +83,17 @@ BatchDev descriptor(const xm_batch_s* b) {
     d.kmax = b->kmax;
     d.budget_ns = (unsigned long long)b->tuning.budget_ms * 1000000ull;
     d.merge_ratio = b->tuning.merge_ratio;
+    d.pair_budget_ns = (unsigned long long)b->pair_budget_ms * 1000000ull;
+    d.pair_t0 = b->d_pair_words;
+    d.pair_status = b->d_pair_words + b->npairs;
     return d;
 }
 
 cudaError_t enqueue(xm_batch_s* b, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(b->d_counts, 0, (size_t)b->npairs * 2 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctl, 0, CTL_WORDS * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->d_pair_words, 0, (size_t)b->npairs * 2 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = launch_batch(descriptor(b), b->tuning.warps_per_block, b->tuning.blocks_per_sm, stream);
     return e;
 }
@@ -152,6 +160,7 @@ int xm_batch_create(int32_t np, const xm_plan* plans, int32_t ng, const xm_graph
     if (e == cudaSuccess) e = dev_alloc(&b->d_prefix, (npairs + 1) * sizeof(long long));
     if (e == cudaSuccess) e = dev_alloc(&b->d_counts, npairs * 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = dev_alloc(&b->d_ctl, CTL_WORDS * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_alloc(&b->d_pair_words, (size_t)npairs * 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_graphs, hg.data(), ng * sizeof(GraphDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_plans, hp.data(), np * sizeof(XmPlanDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_pairs, hpairs.data(), npairs * sizeof(int2), cudaMemcpyHostToDevice);
@@ -288,6 +297,26 @@ int xm_batch_tune(xm_batch b, const xm_tuning* cand, int32_t ncand, int32_t reps
 }
 
 void xm_batch_free(xm_batch b) { free_batch(b); }
+
+int xm_batch_set_pair_budget(xm_batch b, int32_t budget_ms) {
+    if (!b || budget_ms < 0) { set_error("bad per-pair budget"); return XM_EINVAL; }
+    b->pair_budget_ms = budget_ms;
+    drop_graph(b);
+    return XM_OK;
+}
+
+int xm_batch_pair_status(xm_batch b, int32_t* status, void* stream) {
+    if (!b || !status) { set_error("NULL argument"); return XM_EINVAL; }
+    int rc = check_device(b);
+    if (rc) return rc;
+    std::vector<unsigned long long> st(b->npairs);
+    cudaError_t e = cudaMemcpyAsync(st.data(), b->d_pair_words + b->npairs, st.size() * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(e, "pair status readback");
+    for (int64_t i = 0; i < b->npairs; i++) status[i] = (st[i] & STATUS_TIMEOUT) ? XM_ETIMEOUT : XM_OK;
+    return XM_OK;
+}
 
 int xm_count_batch(int32_t np, const xm_plan* plans, int32_t ng, const xm_graph* graphs, int64_t npairs,
                    const int32_t* pair_pg, uint64_t* out_counts, void* stream) {

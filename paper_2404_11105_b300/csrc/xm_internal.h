@@ -52,31 +52,6 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
                     std::string& err, int root = -1);
 std::string describe_plan(const Plan& p);
 
-// Allocator whose resize() leaves new elements uninitialised (large host
-// buffers that are written in full right after, in parallel).
-template <class T>
-struct NoInitAlloc : std::allocator<T> {
-    template <class U>
-    struct rebind { using other = NoInitAlloc<U>; };
-    NoInitAlloc() = default;
-    template <class U>
-    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
-    template <class U, class... A>
-    void construct(U* p, A&&... a) { ::new ((void*)p) U(std::forward<A>(a)...); }
-    template <class U>
-    void construct(U* p) noexcept { ::new ((void*)p) U; }
-};
-template <class T>
-using HostVec = std::vector<T, NoInitAlloc<T>>;
-
-// Host CSR build: dedup, self-loops dropped, ascending lists.
-struct HostCsr {
-    int32_t n = 0;
-    int64_t m = 0;
-    HostVec<int32_t> out_off, out_adj, in_off, in_adj;
-};
-int build_host_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, HostCsr& out, std::string& err);
-
 void set_error(const std::string& msg);
 
 // Every device allocation of the library goes through these: they keep a

@@ -45,31 +45,36 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Work budget of a launch: the first warp to start records the start time
-// in ctl[CTL_T0]; a warp whose check finds the budget spent raises the
-// timeout status bit, and every warp stops at its next check.
+// Work budget of a launch (or of one pair of a batch): the first warp to
+// start records the start time in *t0; a warp whose check finds the budget
+// spent raises the timeout bit in *status, and every warp that checks the
+// same words stops at its next check.
 struct Budget {
     unsigned long long deadline = 0;  // 0: unlimited
-    unsigned long long* ctl = nullptr;
+    unsigned long long* status = nullptr;
     __device__ void start(unsigned long long* c, unsigned long long budget_ns, int lane) {
-        ctl = c;
+        start_at(c + CTL_T0, c + CTL_STATUS, budget_ns, lane);
+    }
+    __device__ void start_at(unsigned long long* t0w, unsigned long long* st, unsigned long long budget_ns, int lane) {
+        status = st;
+        deadline = 0;
         if (!budget_ns) return;
         unsigned long long t0 = 0;
         if (lane == 0) {
             const unsigned long long now = global_ns();
-            const unsigned long long prev = atomicCAS(c + CTL_T0, 0ull, now);
+            const unsigned long long prev = atomicCAS(t0w, 0ull, now);
             t0 = prev ? prev : now;
         }
         deadline = __shfl_sync(FULL, t0, 0) + budget_ns;
     }
-    // true when the launch must stop (warp-uniform)
+    // true when the work must stop (warp-uniform)
     __device__ bool expired(int lane) const {
         if (!deadline) return false;
         int stop = 0;
         if (lane == 0) {
-            stop = (*((volatile unsigned long long*)(ctl + CTL_STATUS)) & STATUS_TIMEOUT) != 0;
+            stop = (*((volatile unsigned long long*)status) & STATUS_TIMEOUT) != 0;
             if (!stop && global_ns() > deadline) {
-                atomicOr(ctl + CTL_STATUS, (unsigned long long)STATUS_TIMEOUT);
+                atomicOr(status, (unsigned long long)STATUS_TIMEOUT);
                 stop = 1;
             }
         }
@@ -132,9 +137,11 @@ __host__ __device__ size_t batch_warp_bytes_impl(int kmax, int window) {
 __host__ __device__ constexpr int n_windows(int k) { return k > 3 ? k - 3 : 0; }
 
 // Per-warp shared memory of k_match: level state, windows of levels
-// 2..k-2, and the merge tile.
-__host__ __device__ constexpr size_t match_warp_bytes(int k, int window) {
-    return warp_state_bytes(k) + (size_t)n_windows(k) * window * sizeof(int32_t) + MERGE_TILE * sizeof(int32_t);
+// 2..k-2, and the merge tile when merging is enabled (shared memory not
+// taken stays L1 cache, which the probe loops live on).
+__host__ __device__ constexpr size_t match_warp_bytes(int k, int window, bool merge) {
+    return warp_state_bytes(k) + (size_t)n_windows(k) * window * sizeof(int32_t) +
+           (merge ? MERGE_TILE * sizeof(int32_t) : 0);
 }
 
 
@@ -158,28 +165,12 @@ __device__ __forceinline__ int lbound(const int32_t* p, int lo, int hi, int32_t 
     return lo;
 }
 
-// Warp-cooperative lower bounds on a sorted list: the first index in
-// [lo, hi) with p[idx] >= x, computed by all 32 lanes together (every lane
-// gets the same result). Each round the lanes read 32 evenly spaced ids of
-// the remaining range and one ballot narrows it 32-fold, so a list of L ids
-// costs about log32(L) + 1 dependent reads instead of log2(L) for one
-// thread. warp_lbound2 runs two searches (x0 over [lo0, hi0), x1 over
-// [lo1, hi1)) in the same rounds, two independent reads per lane.
-__device__ __forceinline__ int warp_lbound(const int32_t* p, int lo, int hi, int32_t x, bool shared, int lane) {
-    while (hi - lo > 32) {
-        const int step = (hi - lo + 31) >> 5;
-        const int q = lo + lane * step;
-        const bool lt = q < hi && ld(p, q, shared) < x;
-        const int c = __popc(__ballot_sync(FULL, lt));
-        if (c == 0) return lo;
-        const int nlo = lo + (c - 1) * step + 1;
-        hi = min(hi, lo + c * step);
-        lo = nlo;
-    }
-    const bool lt = lo + lane < hi && ld(p, lo + lane, shared) < x;
-    return lo + __popc(__ballot_sync(FULL, lt));
-}
-
+// Warp-cooperative lower bounds on a sorted global list, for the
+// instrumented kernel's accounting: the first index in [lo0, hi0) with
+// p[idx] >= x0 and the first in [lo1, hi1) with p[idx] >= x1, computed by
+// all 32 lanes together (every lane gets the results). Each round the lanes
+// read 32 evenly spaced ids of each remaining range and one ballot narrows
+// it 32-fold: about log32(L) + 1 rounds for a list of L ids.
 __device__ __forceinline__ void warp_lbound2(const int32_t* p, int lo0, int hi0, int32_t x0, int lo1, int hi1,
                                              int32_t x1, int& r0, int& r1, int lane) {
     bool d0 = false, d1 = false;
@@ -504,24 +495,24 @@ __global__ void k_units(RunArgs ra) {
 // other): every id is read once, in coalesced 16-byte loads, instead of one
 // random hash-bucket sector per id of the shorter list.
 
-// Lane's MERGE_V ids of the tile of list p that starts at the 16-byte
-// boundary at or below position pos; *t0 receives the tile's first position.
-// Ids at positions before pos read as -1 and at or after end as INT_MAX, so
-// they sort before / after every node id and match nothing real. A 16-byte
-// chunk that holds a position in [pos, end) lies inside the page of that
-// position, so it is read whole; chunks entirely past end are not read.
-__device__ __forceinline__ int4 merge_tile(const int32_t* p, int pos, int end, int lane, int& t0) {
+// Chunk q (16 bytes, four ids) of the tile of list p that starts at the
+// 16-byte boundary at or below position pos; *t0 receives the tile's first
+// position. Ids at positions before pos read as -1 and at or after end as
+// INT_MAX, so they sort before / after every node id and match nothing real.
+// A 16-byte chunk that holds a position in [pos, end) lies inside the page of
+// that position, so it is read whole; chunks entirely past end are not read.
+__device__ __forceinline__ int4 merge_chunk(const int32_t* p, int pos, int end, int q, int& t0) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(p + pos);
     t0 = pos - (int)((a & 15) >> 2);
-    const int q = t0 + 4 * lane;
+    const int e = t0 + 4 * q;  // position of the chunk's first id
     int4 v = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
-    if (q < end) v = __ldg(reinterpret_cast<const int4*>(a & ~uintptr_t(15)) + lane);
-    if (q < pos) v.x = -1;
-    if (q + 1 < pos) v.y = -1;
-    if (q + 2 < pos) v.z = -1;
-    if (q + 1 >= end) v.y = INT_MAX;
-    if (q + 2 >= end) v.z = INT_MAX;
-    if (q + 3 >= end) v.w = INT_MAX;
+    if (e < end) v = __ldg(reinterpret_cast<const int4*>(a & ~uintptr_t(15)) + q);
+    if (e < pos) v.x = -1;
+    if (e + 1 < pos) v.y = -1;
+    if (e + 2 < pos) v.z = -1;
+    if (e + 1 >= end) v.y = INT_MAX;
+    if (e + 2 >= end) v.z = INT_MAX;
+    if (e + 3 >= end) v.w = INT_MAX;
     return v;
 }
 
@@ -531,38 +522,51 @@ __device__ __forceinline__ int32_t int4_at(const int4& v, int j) {
 
 // Number of ids common to the ascending lists A[pa, ea) and B[pb, eb),
 // leaving out the matched nodes m[j] for the bits j of neq (injectivity).
-// Returns this lane's share; the warp's sum is the count. A should be the
-// shorter list. Each round loads one MERGE_TILE-id tile of each list, puts
-// B's into `tile` (shared memory, MERGE_TILE ints of this warp), looks every
-// id of A's tile up in it by binary search, and then advances both lists past
-// the smaller of the two tiles' last ids (one tile is always used up): the
-// merge-path step. Rounds re-read the unused rest of the other tile, which is
-// then in L1.
-__device__ unsigned merge_count(const int32_t* __restrict__ A, int pa, int ea, const int32_t* __restrict__ B, int pb,
-                                int eb, int32_t* tile, uint32_t neq, const int32_t* m, int lane) {
+// Returns this lane's share; the warp's sum is the count. A is the shorter
+// list. Each round loads a 128-id tile of A and a BV x 128-id tile of B
+// (BV chosen from the length ratio, so that both tiles cover about the same
+// id range and every load of the round is in flight at once), puts B's into
+// `tile` (shared memory, MERGE_TILE ints of this warp), looks every id of
+// A's tile up in it by binary search, and then advances both lists past the
+// smaller of the two tiles' last ids (one tile is always used up): the
+// merge-path step. The unused rest of the other tile is read again in the
+// next round, from L1.
+template <int BV>
+__device__ unsigned merge_count_t(const int32_t* __restrict__ A, int pa, int ea, const int32_t* __restrict__ B,
+                                  int pb, int eb, int32_t* tile, uint32_t neq, const int32_t* m, int lane) {
+    constexpr int TB = 128 * BV;
     unsigned cnt = 0;
     while (pa < ea && pb < eb) {
         int ta, tb;
-        const int4 va = merge_tile(A, pa, ea, lane, ta);
-        const int4 vb = merge_tile(B, pb, eb, lane, tb);
+        const int4 va = merge_chunk(A, pa, ea, lane, ta);
+        int4 vb[BV];
+#pragma unroll
+        for (int c = 0; c < BV; c++) vb[c] = merge_chunk(B, pb, eb, lane + 32 * c, tb);
         __syncwarp();
-        reinterpret_cast<int4*>(tile)[lane] = vb;
+#pragma unroll
+        for (int c = 0; c < BV; c++) reinterpret_cast<int4*>(tile)[lane + 32 * c] = vb[c];
         __syncwarp();
-        const int la = min(ea, ta + MERGE_TILE) - 1 - ta;  // tile index of A's last real id
-        const int lb = min(eb, tb + MERGE_TILE) - 1 - tb;
+        const int la = min(ea, ta + 128) - 1 - ta;  // tile index of A's last real id
+        const int lb = min(eb, tb + TB) - 1 - tb;
         const int32_t lastA = __shfl_sync(FULL, int4_at(va, la & 3), la >> 2);
         const int32_t lim = min(lastA, tile[lb]);
         int na = 0, nb = 0;
 #pragma unroll
+        for (int c = 0; c < BV; c++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int32_t y = int4_at(vb[c], j);
+                nb += __popc(__ballot_sync(FULL, y >= 0 && y <= lim));
+            }
+#pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int32_t x = int4_at(va, j), y = int4_at(vb, j);
+            const int32_t x = int4_at(va, j);
             const bool ok = x >= 0 && x <= lim;
             na += __popc(__ballot_sync(FULL, ok));
-            nb += __popc(__ballot_sync(FULL, y >= 0 && y <= lim));
             if (ok) {
-                int i = 0;  // number of tile ids below x (at most MERGE_TILE - 1)
+                int i = 0;  // number of tile ids below x (at most TB - 1)
 #pragma unroll
-                for (int s = MERGE_TILE / 2; s > 0; s >>= 1)
+                for (int s = TB / 2; s > 0; s >>= 1)
                     if (tile[i + s - 1] < x) i += s;
                 bool f = tile[i] == x;
                 for (uint32_t nm = neq; nm && f; nm &= nm - 1) f = x != m[__ffs(nm) - 1];
@@ -573,6 +577,14 @@ __device__ unsigned merge_count(const int32_t* __restrict__ A, int pa, int ea, c
         pb += nb;
     }
     return cnt;
+}
+
+__device__ __forceinline__ unsigned merge_count(const int32_t* A, int pa, int ea, const int32_t* B, int pb, int eb,
+                                                int32_t* tile, uint32_t neq, const int32_t* m, int lane) {
+    const long long na = ea - pa, nb = eb - pb;
+    if (nb >= 3 * na) return merge_count_t<4>(A, pa, ea, B, pb, eb, tile, neq, m, lane);
+    if (nb >= 2 * na) return merge_count_t<2>(A, pa, ea, B, pb, eb, tile, neq, m, lane);
+    return merge_count_t<1>(A, pa, ea, B, pb, eb, tile, neq, m, lane);
 }
 
 // ----------------------------------------------------------------- k_match
@@ -663,8 +675,8 @@ __device__ void setup_lists(const XmLevel& L, const GraphDev& g, WarpSmem& ws, L
     }
     int c0 = 0, c1 = lists[d].len;
     if (!empty) {
-        if (lo >= 0) c0 = warp_lbound(lists[d].p, 0, c1, lo + 1, lists[d].shared, lane);
-        if (hi != INT_MAX) c1 = warp_lbound(lists[d].p, c0, c1, hi, lists[d].shared, lane);
+        if (lo >= 0) c0 = lbound(lists[d].p, 0, c1, lo + 1, lists[d].shared);
+        if (hi != INT_MAX) c1 = lbound(lists[d].p, c0, c1, hi, lists[d].shared);
     }
     if (c0 >= c1) empty = true;
     if (lane == 0) {
@@ -841,7 +853,7 @@ __device__ unsigned long long leaf_count_hashed(const XmLevel& L, WarpSmem& ws, 
 // probe list is cut to the driver range's ids; when that cut is at most
 // ra.merge_ratio times the driver range both are merged, else the driver's
 // ids probe the list's hash table.
-template <int MODE>
+template <int MODE, bool LEAN = false>
 __device__ unsigned long long leaf_tail(const XmPlanDev& P, const XmLevel& L, const GraphDev& g, WarpSmem& ws,
                                         LvState& S, int l, int lane, const RunArgs& ra, Stats& st, int pos, int end) {
     if (MODE == MODE_STATS && lane == 0) st.leaf += end - pos;
@@ -870,7 +882,7 @@ __device__ unsigned long long leaf_tail(const XmPlanDev& P, const XmLevel& L, co
                          eb, lane);
             cut0 = eb - pb;
         }
-        if (S.nprobe == 1 && global && ra.merge_ratio > 0 && run >= MERGE_MIN_RUN &&
+        if (!LEAN && S.nprobe == 1 && global && ra.merge_ratio > 0 && run >= MERGE_MIN_RUN &&
             (long long)S.phi[0] <= (long long)ra.merge_ratio * run) {
             // the whole probe list is within the ratio: merged whole, no cut
             if (MODE == MODE_STATS && lane == 0) {
@@ -899,7 +911,7 @@ __device__ unsigned long long leaf_tail(const XmPlanDev& P, const XmLevel& L, co
 
 // Count (or emit) the candidates of the last level l >= 2, optionally only
 // the sub-range [c0 + ra_pos, c0 + ra_pos + ra_len) of its cut driver range.
-template <int MODE>
+template <int MODE, bool LEAN = false>
 __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int l, int lane,
                                          const RunArgs& ra, Stats& st, int ra_pos = 0, int ra_len = -1) {
     setup_level<MODE>(P, g, ws, l, lane, st, false);
@@ -908,7 +920,7 @@ __device__ unsigned long long leaf_level(const XmPlanDev& P, const GraphDev& g, 
     const int pos = ra_len < 0 ? S.c0 : min(S.c1, S.c0 + ra_pos);
     const int end = ra_len < 0 ? S.c1 : min(S.c1, pos + ra_len);
     if (pos >= end) return 0;
-    return leaf_tail<MODE>(P, P.lv[l], g, ws, S, l, lane, ra, st, pos, end);
+    return leaf_tail<MODE, LEAN>(P, P.lv[l], g, ws, S, l, lane, ra, st, pos, end);
 }
 
 // Plans whose last level k - 1 intersects exactly two operand lists, one of
@@ -1179,13 +1191,13 @@ __device__ bool descend(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
 // the last level is counted (or emitted) into acc. With PROD (counting with
 // a leaf product, sets ra.pv) the walk ends at level prod_p, which adds the
 // product (values past 64 bits go straight to *counter).
-template <int MODE, bool PROD>
+template <int MODE, bool PROD, bool LEAN = false>
 __device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* wins, int W, int wl0, int lane,
                         const RunArgs& ra, unsigned long long& acc, unsigned long long* counter, Stats& st,
                         const Budget& budget, int l0 = 1) {
     const int k = PROD ? P.prod_p + 1 : P.k;
     // two-list last levels are counted a batch of candidates at a time
-    const int iF = (!PROD && MODE != MODE_EMIT) ? batch_leaf_fixed_op(P) : -1;
+    const int iF = (!PROD && !LEAN && MODE != MODE_EMIT) ? batch_leaf_fixed_op(P) : -1;
     int l = l0;
     unsigned steps = 0;
     while (l >= l0) {
@@ -1221,7 +1233,7 @@ __device__ bool explore(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int
             if (PROD)
                 add_count(acc, leaf_product<MODE>(P, ra.pv, g, ws, l + 1, lane, ra, st), counter, lane);
             else
-                acc += leaf_level<MODE>(P, g, ws, l + 1, lane, ra, st);
+                acc += leaf_level<MODE, LEAN>(P, g, ws, l + 1, lane, ra, st);
             if (MODE == MODE_STATS && lane == 0) st.sets++;
             continue;
         }
@@ -1248,10 +1260,10 @@ __device__ __forceinline__ void flush_count(unsigned long long acc, unsigned lon
 }
 
 // Guided self-scheduling: lane 0 takes a batch of units proportional to
-// what is left; returns [start, start + cnt) on every lane (cnt <= 0: done,
-// or the budget is spent).
+// what is left, at most maxb; returns [start, start + cnt) on every lane
+// (cnt <= 0: done, or the budget is spent).
 __device__ __forceinline__ void grab_units(unsigned long long* head, long long total, int nwarps, int lane,
-                                           long long& start, int& cnt, const Budget& budget) {
+                                           long long& start, int& cnt, const Budget& budget, int maxb = 64) {
     if (budget.expired(lane)) {
         start = total;
         cnt = 0;
@@ -1262,7 +1274,7 @@ __device__ __forceinline__ void grab_units(unsigned long long* head, long long t
     if (lane == 0) {
         unsigned long long seen = *((volatile unsigned long long*)head);
         long long left = total - (long long)seen;
-        int batch = left > 0 ? (int)min(64ll, max(1ll, left / (8ll * nwarps))) : 1;
+        int batch = left > 0 ? (int)min((long long)maxb, max(1ll, left / (8ll * nwarps))) : 1;
         unsigned long long s = atomicAdd(head, (unsigned long long)batch);
         s0 = (long long)s >= total ? total : (long long)s;
         c = (int)min((long long)batch, total - s0);
@@ -1316,22 +1328,48 @@ __device__ void level2_cut(const XmPlanDev& P, const GraphDev& g, int32_t m0, in
     if (empty || c1 < c0) c1 = c0;
 }
 
+// Second-level driver positions per work unit below the first-level node m1
+// of start node m0, for a walk of ke levels: LEAF_UNIT when the second level
+// is the last; for four levels whose last one intersects a list of node m0
+// or m1 (the same for every leaf of the unit) with the leaf candidate's own
+// list, fewer when that common list is longer than HEAVY_LIST ids -- each
+// leaf costs about its length, and a hub's leaves would otherwise stay
+// together in one warp; else `unit`.
+__device__ __forceinline__ int l2_piece(const XmPlanDev& P, const GraphDev& g, int ke, int unit, int32_t m0,
+                                        int32_t m1) {
+    if (ke == 3) return LEAF_UNIT;
+    if (ke == 4 && P.k == 4) {
+        const int iF = batch_leaf_fixed_op(P);
+        if (iF >= 0) {
+            const XmLevel& L = P.lv[3];
+            const int32_t v = L.op_level[iF] ? m1 : m0;
+            const int32_t* off = L.op_dir[iF] == XM_DIR_OUT ? g.out_off : g.in_off;
+            const long long len = __ldg(off + v + 1) - __ldg(off + v);
+            if (len > HEAVY_LIST) return max(1, (int)((long long)unit * HEAVY_LIST / len));
+        }
+    }
+    return unit;
+}
+
 // Work units per first-level candidate (patterns of three or more
-// vertices): its second-level driver range cut into pieces, so the work
-// below one hub is spread over many warps. One thread per candidate.
+// vertices): its second-level driver range cut into pieces (l2_piece), so
+// the work below one hub is spread over many warps. One thread per
+// candidate.
 __global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     __shared__ __align__(16) unsigned char pbuf[plan_bytes(XM_MAXK)];
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(pbuf);
     plan_to_smem(P, plan_g);
     const int E = set_start(ra, ra.n_idx);
-    const int per = P.k == 3 ? LEAF_UNIT : ra.unit;
+    const int ke = ra.pv ? P.prod_p + 1 : P.k;  // levels the count walks
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= ra.emax; e += gridDim.x * blockDim.x) {
         int u = 0;
         if (e < E) {
             const int i = __ldg(ra.l1root + e);
             const int s0 = set_start(ra, i), s1 = set_start(ra, i + 1);
+            const int32_t m0 = root_node(ra, i), m1 = __ldg(ra.l1set + e);
             int c0, c1;
-            level2_cut(P, ra.g, root_node(ra, i), __ldg(ra.l1set + e), ra.l1set + s0, s1 - s0, c0, c1);
+            level2_cut(P, ra.g, m0, m1, ra.l1set + s0, s1 - s0, c0, c1);
+            const int per = l2_piece(P, ra.g, ke, ra.unit, m0, m1);
             u = (c1 - c0 + per - 1) / per;
         }
         ra.e_units[e] = u;
@@ -1349,7 +1387,7 @@ __global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
 // Returns false (nothing counted) when the level needs the general path:
 // difference lists, more than two probe lists, or a probe without a hash
 // table that is not merged. Survivors are counted per lane into acc.
-template <int MODE>
+template <int MODE, bool LEAN>
 __device__ __forceinline__ bool leaf3_direct(const XmPlanDev& P, const GraphDev& g, int32_t m0, int32_t m1,
                                              const int32_t* set, int set_len, int pos0, int per, int lane,
                                              unsigned long long& acc, const RunArgs& ra, WarpSmem& ws, Stats& st) {
@@ -1403,7 +1441,7 @@ __device__ __forceinline__ bool leaf3_direct(const XmPlanDev& P, const GraphDev&
         if (np == 0) psrc = i;
         np++;
     }
-    const bool try_merge = np == 1 && ra.merge_ratio > 0;
+    const bool try_merge = !LEAN && np == 1 && ra.merge_ratio > 0;
     if (!hashed && !try_merge) return false;
     const int32_t* dp =
         dsrc == -1 ? set
@@ -1417,8 +1455,8 @@ __device__ __forceinline__ bool leaf3_direct(const XmPlanDev& P, const GraphDev&
     int32_t lo, hi;
     level_bounds(L, m, lo, hi);
     int c0 = 0, c1 = dlen;
-    if (lo >= 0) c0 = warp_lbound(dp, 0, c1, lo + 1, false, lane);
-    if (hi != INT_MAX) c1 = warp_lbound(dp, c0, c1, hi, false, lane);
+    if (lo >= 0) c0 = lbound(dp, 0, c1, lo + 1, false);
+    if (hi != INT_MAX) c1 = lbound(dp, c0, c1, hi, false);
     if (MODE == MODE_STATS && lane == 0) {
         const int ns = (lo >= 0 ? 1 : 0) + (hi != INT_MAX ? 1 : 0);
         st.bytes += ns * search_bytes(dlen);
@@ -1449,7 +1487,7 @@ __device__ __forceinline__ bool leaf3_direct(const XmPlanDev& P, const GraphDev&
         return true;
     }
     long long cut0 = -1;
-    if (np == 1) {
+    if (!LEAN && np == 1) {
         const int32_t* B = reinterpret_cast<const int32_t*>(
             __shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.p), psrc));
         const int blen = plen[0];
@@ -1580,8 +1618,15 @@ __device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDe
 // or the node id without one), ra.root_counts[2 i .. 2 i + 1]. (A run-time
 // switch: a third template flag for it made ptxas fail on the product
 // kernel.)
-template <int MODE, bool PROD>
-__global__ void __launch_bounds__(512, 2) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+// MINB: resident 512-thread blocks the register budget must allow -- 3 (40
+// registers a thread, 48 warps an SM) for three-level plans, whose probe
+// loops are latency-bound and want warps; 2 (64 registers) for deeper
+// plans, whose batched last level needs the registers.
+template <int MODE, bool PROD, int MINB = 2>
+__global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
+    // the three-level build leaves out the batched last level and the
+    // merges (their registers would spill into its probe loops)
+    constexpr bool LEAN = MINB >= 3;
     const bool ROOTS = MODE == MODE_COUNT && ra.root_counts != nullptr;
     extern __shared__ __align__(16) unsigned char smem[];
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(smem);
@@ -1594,11 +1639,12 @@ __global__ void __launch_bounds__(512, 2) k_match(const XmPlanDev* __restrict__ 
     constexpr bool prod = PROD;
     const int ke = prod ? P.prod_p + 1 : k;
     const int W = ra.window;
-    const size_t warp_bytes = match_warp_bytes(k, W);
+    const bool tile = !LEAN && ra.merge_ratio > 0;
+    const size_t warp_bytes = match_warp_bytes(k, W, tile);
     unsigned char* wbase = smem + plan_bytes(k) + (size_t)wib * warp_bytes;
     WarpSmem& ws = *reinterpret_cast<WarpSmem*>(wbase);
     int32_t* wins = reinterpret_cast<int32_t*>(wbase + warp_state_bytes(k));  // level l >= 2 at (l-2)*W
-    if (lane == 0) ws.mtile = wins + (size_t)n_windows(k) * W;
+    if (lane == 0) ws.mtile = tile ? wins + (size_t)n_windows(k) * W : nullptr;
     __syncwarp();
     const GraphDev& g = ra.g;
     const bool two_level = !ra.l2_units;
@@ -1608,7 +1654,10 @@ __global__ void __launch_bounds__(512, 2) k_match(const XmPlanDev* __restrict__ 
     const int nidx = two_level ? ra.n_idx : ra.emax;
     const int total = uprefix[nidx];
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int per2 = ke == 3 ? LEAF_UNIT : ra.unit;
+    // walks of four or more levels: the units of one heavy start node lie
+    // next to each other and cost far more than the average, so warps take
+    // them two at a time (a batch of them would end up in one warp)
+    const int maxb = ke >= 4 ? 2 : 64;
 
     unsigned long long acc = 0;
     Stats st;
@@ -1621,7 +1670,7 @@ __global__ void __launch_bounds__(512, 2) k_match(const XmPlanDev* __restrict__ 
     for (;;) {
         long long start;
         int cnt;
-        grab_units(ra.ctl + CTL_HEAD, total, nwarps, lane, start, cnt, budget);
+        grab_units(ra.ctl + CTL_HEAD, total, nwarps, lane, start, cnt, budget, maxb);
         if (cnt <= 0) break;
         bool stop = false;
         for (int u = (int)start; u < (int)start + cnt && !stop; u++) {
@@ -1678,7 +1727,8 @@ __global__ void __launch_bounds__(512, 2) k_match(const XmPlanDev* __restrict__ 
                     S1.drv_pos = S1.drv_end = 0;
                 }
                 __syncwarp();
-                if (!explore<MODE, PROD>(P, g, ws, wins, W, 2, lane, ra, acc, counter, st, budget, 1)) stop = true;
+                if (!explore<MODE, PROD, LEAN>(P, g, ws, wins, W, 2, lane, ra, acc, counter, st, budget, 1))
+                    stop = true;
                 continue;
             }
             if (two_level) {
@@ -1710,12 +1760,13 @@ __global__ void __launch_bounds__(512, 2) k_match(const XmPlanDev* __restrict__ 
             const int e = owner;
             const int root = __ldg(ra.l1root + e);
             const int s0 = set_start(ra, root), s1 = set_start(ra, root + 1);
+            const int per2 = l2_piece(P, g, ke, ra.unit, root_node(ra, root), __ldg(ra.l1set + e));
             if (MODE == MODE_STATS && lane == 0) {
                 st.bytes += 4;
                 st.touched += 4;
             }
             if (MODE != MODE_EMIT && ke == 3 &&
-                leaf3_direct<MODE>(P, g, root_node(ra, root), __ldg(ra.l1set + e), ra.l1set + s0, s1 - s0,
+                leaf3_direct<MODE, LEAN>(P, g, root_node(ra, root), __ldg(ra.l1set + e), ra.l1set + s0, s1 - s0,
                                    chunk * per2, per2, lane, acc, ra, ws, st))
                 continue;
             if (lane == 0) {
@@ -1732,7 +1783,7 @@ __global__ void __launch_bounds__(512, 2) k_match(const XmPlanDev* __restrict__ 
             __syncwarp();
             if (MODE == MODE_STATS && lane == 0) st.ext++;
             if (ke == 3) {
-                acc += leaf_level<MODE>(P, g, ws, 2, lane, ra, st, chunk * per2, per2);
+                acc += leaf_level<MODE, LEAN>(P, g, ws, 2, lane, ra, st, chunk * per2, per2);
                 if (MODE == MODE_STATS && lane == 0) st.sets++;
                 continue;
             }
@@ -1763,7 +1814,7 @@ __global__ void __launch_bounds__(512, 2) k_match(const XmPlanDev* __restrict__ 
                 S2.set_shared = 1;
             }
             __syncwarp();
-            if (!explore<MODE, PROD>(P, g, ws, wins, W, 2, lane, ra, acc, counter, st, budget, 2)) stop = true;
+            if (!explore<MODE, PROD, LEAN>(P, g, ws, wins, W, 2, lane, ra, acc, counter, st, budget, 2)) stop = true;
         }
         if (stop) break;
     }
@@ -1814,6 +1865,7 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
     int cur = -1;
     unsigned long long acc = 0;
     bool stop = false;
+    Budget pair_budget;  // per-pair budgets: the current pair's
     for (; !stop;) {
         long long start;
         int cnt;
@@ -1840,10 +1892,15 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
                     reinterpret_cast<int32_t*>(&P)[i] = reinterpret_cast<const int32_t*>(b.plans + pg.x)[i];
                 g = b.graphs[pg.y];
                 __syncwarp();
+                if (b.pair_budget_ns)
+                    pair_budget.start_at(b.pair_t0 + cur, b.pair_status + cur, b.pair_budget_ns, lane);
             }
+            // a pair over its own budget: its remaining units are skipped
+            if (b.pair_budget_ns && pair_budget.expired(lane)) continue;
             const int r0 = (int)(u - __ldg(b.unit_prefix + cur)) * b.root_block;
             const int r1 = min(r0 + b.root_block, g.n);
             const int k = P.k;
+            const Budget& bud = b.pair_budget_ns ? pair_budget : budget;
             for (int v = r0; v < r1; v++) {
                 if (!passes_degree(g, v, P.lv[0].dout_min, P.lv[0].din_min)) continue;
                 if (lane == 0) ws.m[0] = v;
@@ -1854,8 +1911,8 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
                 }
                 if (!descend<MODE_COUNT>(P, g, ws, wins, W, 1, lane, ra, st)) continue;
                 if (!explore<MODE_COUNT, false>(P, g, ws, wins, W, 1, lane, ra, acc, b.counts + 2 * (size_t)cur, st,
-                                                budget)) {
-                    stop = true;
+                                                bud)) {
+                    stop = !b.pair_budget_ns;  // a pair's budget ends that pair only
                     break;
                 }
             }
@@ -2002,7 +2059,13 @@ cudaError_t scan_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_
 
 size_t batch_warp_bytes(int kmax, int window) { return batch_warp_bytes_impl(kmax, window); }
 
-size_t match_smem_bytes(int k, int window, int warps) { return plan_bytes(k) + match_warp_bytes(k, window) * warps; }
+cudaError_t scan_int32_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_t stream) {
+    return scan_in_place(v, len, a, stream);
+}
+
+size_t match_smem_bytes(int k, int window, int warps, bool merge) {
+    return plan_bytes(k) + match_warp_bytes(k, window, merge) * warps;
+}
 
 int64_t chunk_capacity(int32_t n, int64_t m) { return (int64_t)n + (m + L1_CHUNK - 1) / L1_CHUNK; }
 
@@ -2097,14 +2160,18 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // 3. persistent matcher
-    const size_t smem = match_smem_bytes(P.k, b.window, warps_per_block);
     const bool prod = b.pv != nullptr;
     const bool roots = b.root_counts != nullptr;
     if (roots && mode != MODE_COUNT) return cudaErrorInvalidValue;
+    // three-level counts (the last level probed from registers) run the
+    // 40-register build, which never merges
+    const bool three = mode == MODE_COUNT && !prod && P.k == 3;
+    const size_t smem = match_smem_bytes(P.k, b.window, warps_per_block, b.merge_ratio > 0 && !three);
     const void* fn = mode == MODE_STATS  ? (prod ? (const void*)k_match<MODE_STATS, true>
                                                  : (const void*)k_match<MODE_STATS, false>)
                      : mode == MODE_EMIT ? (const void*)k_match<MODE_EMIT, false>
                      : prod              ? (const void*)k_match<MODE_COUNT, true>
+                     : three             ? (const void*)k_match<MODE_COUNT, false, 3>
                                          : (const void*)k_match<MODE_COUNT, false>;
     if ((err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return err;
@@ -2123,6 +2190,8 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
         k_match<MODE_EMIT, false><<<grid, block, smem, stream>>>(plan_dev, b);
     else if (prod)
         k_match<MODE_COUNT, true><<<grid, block, smem, stream>>>(plan_dev, b);
+    else if (three)
+        k_match<MODE_COUNT, false, 3><<<grid, block, smem, stream>>>(plan_dev, b);
     else
         k_match<MODE_COUNT, false><<<grid, block, smem, stream>>>(plan_dev, b);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -46,18 +46,19 @@ __host__ __device__ __forceinline__ uint32_t hash_bucket(int32_t x, uint32_t nbu
 
 // Table size in slots for a list of `len` ids (0: no table): a power of two
 // at least twice the length, so tables are at most half full.
-inline uint32_t hash_table_size(int64_t len) {
+__host__ __device__ inline uint32_t hash_table_size(int64_t len) {
     if (len < HASH_MIN_LEN) return 0;
     uint32_t t = HASH_BUCKET;
     while ((int64_t)t < 2 * len) t <<= 1;
     return t;
 }
 
-// Ids per tile of the merge intersection: 32 lanes x one 16-byte load.
-constexpr int MERGE_TILE = 128;
+// Ids of the longer list's tile of the merge intersection (shared memory
+// per warp): up to four 16-byte loads per lane.
+constexpr int MERGE_TILE = 512;
 // Default list-length ratio below which two lists are merged instead of
 // probing the longer one once per id of the shorter (RunArgs::merge_ratio).
-constexpr int MERGE_RATIO_DEFAULT = 8;
+constexpr int MERGE_RATIO_DEFAULT = 2;
 // Shorter lists than this are never merged: one round of probes costs less
 // than the merge's per-tile rounds.
 constexpr int MERGE_MIN_RUN = 64;
@@ -118,7 +119,7 @@ struct RunArgs {
 };
 
 enum { MODE_COUNT = 0, MODE_STATS = 1, MODE_EMIT = 2 };
-enum { STATUS_OVERFLOW = 1, STATUS_TIMEOUT = 2 };
+enum { STATUS_OVERFLOW = 1, STATUS_TIMEOUT = 2, STATUS_BAD_ID = 4 };
 
 // Descriptor of a batched launch (device pointers).
 struct BatchDev {
@@ -134,6 +135,9 @@ struct BatchDev {
     unsigned long long budget_ns;    // time budget (0: none)
     int32_t kmax;                    // largest pattern in the batch
     int32_t merge_ratio;             // as RunArgs::merge_ratio
+    unsigned long long pair_budget_ns = 0;  // per-pair budget (0: none)
+    unsigned long long* pair_t0 = nullptr;      // per pair: global timer when its first unit started
+    unsigned long long* pair_status = nullptr;  // per pair: STATUS_TIMEOUT when its budget ran out
 };
 
 // Shared memory per warp of the batched matcher.
@@ -144,17 +148,49 @@ cudaError_t launch_batch(const BatchDev& b, int warps_per_block, int blocks_per_
 
 // Tile of the in-place scans (elements per block).
 constexpr int SCAN_TILE = 4096;
+
+// Exclusive scan of int32 v[0..len) in place, with the partials and status
+// word of a (block_sums: at least ceil(len / SCAN_TILE) entries; ctl).
+cudaError_t scan_int32_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_t stream);
+
+// Device construction of the dual CSR (xm_csr_device.cu).
+// Bits b of one key half (2^b >= n).
+int csr_key_bits(int32_t n);
+// int32 scratch the build needs for m input arcs and n nodes.
+int64_t csr_int_scratch(int64_t m, int32_t n);
+// Sorts the packed (src, dst) keys of the m input arcs (device arrays) and
+// keeps one copy of every arc that is not a self-loop: *keys_out (k0 or k1,
+// each m keys) holds the *m_out distinct keys in ascending order.
+// Synchronises `stream` once (the distinct count).
+cudaError_t csr_sort_unique(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, unsigned long long* k0,
+                            unsigned long long* k1, int32_t* ints, const RunArgs& sa, unsigned long long** keys_out,
+                            int64_t* m_out, cudaStream_t stream);
+// From the mm distinct ascending keys: out_off/out_adj, then in_off/in_adj
+// (the keys with halves swapped, sorted; `spare` holds mm keys, `keys` is
+// overwritten).
+cudaError_t csr_emit(int32_t n, unsigned long long* keys, unsigned long long* spare, int64_t mm, int32_t* ints,
+                     const RunArgs& sa, int32_t* out_off, int32_t* out_adj, int32_t* in_off, int32_t* in_adj,
+                     cudaStream_t stream);
+// Per-node hash-table offsets of one CSR side: hoff[v] = slots of the
+// tables of nodes < v (hash_table_size of each list), using ints[n + 1].
+cudaError_t hash_offsets(const int32_t* off, int32_t n, int32_t* ints, const RunArgs& sa, int64_t* hoff,
+                         cudaStream_t stream);
 // First-level driver positions per chunk of the first-level set build.
 constexpr int L1_CHUNK = 1024;
 // Second-level driver positions per work unit when the second level is the
 // last one (three-vertex patterns): leaf intersections are cheap per id.
 constexpr int LEAF_UNIT = 1024;
 
+// Common last-level lists longer than this shrink the work units of
+// four-level walks (l2_piece).
+constexpr int HEAVY_LIST = 4096;
+
 // Upper bound on the number of first-level chunks of a graph.
 int64_t chunk_capacity(int32_t n, int64_t m);
 
-// Bytes of shared memory a block of `warps` warps needs.
-size_t match_smem_bytes(int k, int window, int warps);
+// Bytes of shared memory a block of `warps` warps needs (merge: with the
+// per-warp merge tiles, when the tuning lets last levels merge).
+size_t match_smem_bytes(int k, int window, int warps, bool merge);
 
 // Whether a plan's work units split below the first level (RunArgs::l2_units)
 // for a counting (count/stats) or an enumerating pass.

@@ -54,7 +54,7 @@ def test_batch_tunings_graph_replay_and_autotuner(xm, setup):
     assert b.counts() == ref
     best, ms = b.tune([(128, 16, 4, 0, 0), (256, 64, 8, 0, 0), (64, 4, 8, 2, 0)], reps=2)
     launch = {k: best[k] for k in ("window", "unit", "warps_per_block", "blocks_per_sm", "budget_ms")}
-    assert ms > 0 and best["merge_ratio"] == 8 and launch in (
+    assert ms > 0 and best["merge_ratio"] == 2 and launch in (
         {"window": 128, "unit": 16, "warps_per_block": 4, "blocks_per_sm": 0, "budget_ms": 0},
         {"window": 256, "unit": 64, "warps_per_block": 8, "blocks_per_sm": 0, "budget_ms": 0},
         {"window": 64, "unit": 4, "warps_per_block": 8, "blocks_per_sm": 2, "budget_ms": 0})
@@ -67,3 +67,31 @@ def test_batch_rejects_bad_pairs(xm, setup):
     pats, xg, og, xp, pairs = setup
     with pytest.raises(xm.XmError):
         xm.Batch(xp, xg, [(0, len(xg))])
+
+
+def test_batch_per_pair_budget(xm, setup):
+    """With a per-pair budget, a pair that needs far more than its budget is
+    reported as timed out while every other pair of the same launch keeps
+    its exact count; without a budget every pair reports XM_OK."""
+    pats, xg, og, xp, pairs = setup
+    n, src, dst = synth.rmat_graph(14, 16, seed=5)
+    heavy_g = xm.Graph(n, src, dst)
+    heavy_p = xm.Plan(synth.transitive_tournament(6))
+    graphs = xg + [heavy_g]
+    plans = xp + [heavy_p]
+    hp = [(len(plans) - 1, len(graphs) - 1)] + pairs
+    want = xm.xm_count_batch(xp, xg, pairs)
+    b = xm.Batch(plans, graphs, hp)
+    b.set_pair_budget(1)
+    b.run()
+    counts = b.counts()
+    st = b.pair_status()
+    assert st[0] == xm.XM_ETIMEOUT
+    assert (st[1:] == xm.XM_OK).all()
+    assert counts[1:] == want
+    b.free()
+    light = xm.Batch(xp, xg, pairs)
+    light.set_pair_budget(0)
+    light.run()
+    assert (light.pair_status() == xm.XM_OK).all() and light.counts() == want
+    light.free()

@@ -115,9 +115,9 @@ def test_shared_endpoints_are_reduced():
 def test_tuning_roundtrip_and_validation():
     p = xm.Plan(synth.BIFAN)
     p.set_tuning(window=256, unit=16, warps_per_block=4, blocks_per_sm=2)
-    # merge_ratio 0 resolves to the default length ratio (8)
+    # merge_ratio 0 resolves to the default length ratio (2)
     assert p.tuning() == {"window": 256, "unit": 16, "warps_per_block": 4, "blocks_per_sm": 2, "budget_ms": 0,
-                          "merge_ratio": 8}
+                          "merge_ratio": 2}
     p.set_tuning(merge_ratio=-1)
     assert p.tuning()["merge_ratio"] == -1
     p.set_tuning(merge_ratio=1024)

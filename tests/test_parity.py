@@ -229,6 +229,52 @@ def test_edge_cases(xm):
         assert xm.xm_count(g, xm.Plan(pat)) == og.count_matches(pat)
 
 
+def _oracle_dual_csr(og):
+    """The oracle's sorted adjacency as out- and in-CSR (the in-lists as
+    the transpose of its out-lists)."""
+    off, adj = og.out_csr()
+    src = np.repeat(np.arange(og.n, dtype=np.int64), np.diff(off))
+    order = np.lexsort((src, adj))
+    in_adj = src[order].astype(np.int32)
+    in_off = np.concatenate([[0], np.cumsum(np.bincount(adj, minlength=og.n))]).astype(np.int64)
+    return off, adj, in_off, in_adj
+
+
+def test_device_csr_build_against_oracle(xm):
+    """The dual CSR built on the device (radix sort of packed arcs, repeats and
+    self-loops dropped) equals the oracle's adjacency: skewed and uniform
+    graphs with repeats and self-loops, a node without arcs, only loops,
+    no arcs, device-pointer input, several builds in a row."""
+    rng = np.random.default_rng(11)
+    cases = [synth.rmat_graph(12, 8, seed=3), synth.er_graph(3000, 40000, seed=5)]
+    n, s_, d_ = synth.rmat_graph(10, 16, seed=9)
+    cases.append((n, np.concatenate([s_, s_[:5000], np.arange(50, dtype=np.int32)]),
+                  np.concatenate([d_, d_[:5000], np.arange(50, dtype=np.int32)])))  # repeats and loops
+    cases.append((7, np.array([0, 1, 2, 2, 5], np.int32), np.array([1, 0, 2, 5, 2], np.int32)))  # node 6 isolated
+    cases.append((4, np.array([1, 1, 3], np.int32), np.array([1, 1, 3], np.int32)))             # only loops
+    cases.append((9, np.zeros(0, np.int32), np.zeros(0, np.int32)))                               # no arcs
+    cases.append((1 << 15, rng.integers(0, 1 << 15, 200000).astype(np.int32),
+                  rng.integers(0, 1 << 15, 200000).astype(np.int32)))
+    for i, (n, src, dst) in enumerate(cases + cases[:2]):
+        og = oracle.OracleGraph(n, src, dst)
+        want = _oracle_dual_csr(og)
+        for dev in ((False, True) if i == 0 else (False,)):
+            a, b = (torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda()) if dev else (src, dst)
+            g = xm.Graph(n, a, b)
+            assert g.m == og.m, i
+            for got, w, name in zip(g.csr_host(), want, ("out_off", "out_adj", "in_off", "in_adj")):
+                assert np.array_equal(got.astype(np.int64), np.asarray(w, np.int64)), (i, name)
+            g.free()
+    # an endpoint outside [0, n) is refused, for host and device arrays
+    for dev in (False, True):
+        s_bad = np.array([0, 1, 5], np.int32)
+        d_bad = np.array([1, 2, 0], np.int32)
+        a, b = (torch.from_numpy(s_bad).cuda(), torch.from_numpy(d_bad).cuda()) if dev else (s_bad, d_bad)
+        with pytest.raises(xm.XmError) as ei:
+            xm.Graph(4, a, b)
+        assert ei.value.status == xm.XM_EINVAL
+
+
 def test_device_pointer_input(xm):
     n, src, dst = synth.er_graph(800, 9000, seed=12)
     g1 = xm.Graph(n, src, dst)
@@ -433,7 +479,7 @@ def test_plan_autotuner(xm, rmat_small):
     want = og.count_matches(synth.BIFAN)
     cands = [(64, 1, 2, 0, 0), (256, 8, 8, 0, 0), (512, 32, 4, 1, 0)]
     best, ms = xm.xm_plan_tune(g, p, cands, reps=2)
-    assert ms > 0 and tuple(best.values())[:5] in cands and best["merge_ratio"] == 8
+    assert ms > 0 and tuple(best.values())[:5] in cands and best["merge_ratio"] == 2
     assert p.tuning() == best
     assert xm.xm_count(g, p) == want
     # on a start-node list, with the intersection strategy as a knob
