@@ -387,7 +387,12 @@ int xm_count(xm_graph g, xm_plan p, uint64_t *lo, uint64_t *hi, void *stream);
  * vertex (xm_plan_info's `start`) is mapped to a node in [root_lo, root_hi)
  * (Alg. 2 parallelises over the start vertex's candidates). Counts over a
  * partition of [0, n) add up to xm_count. Ranges are clipped to [0, n).
- * Uses the leaf product but never the cut-vertex decomposition.
+ * Uses the leaf product, and the cut-vertex decomposition when its cut
+ * vertex is the start vertex and every automorphism of the pattern fixes
+ * it (xm_plan_describe: "start-node subsets split"): then all embeddings of
+ * a match map the cut vertex to the same node, so the per-node form of the
+ * split identity holds, with the quotient patterns counted rooted at the
+ * cut vertex over the same start nodes. Otherwise the plan is walked.
  */
 int xm_count_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t *lo, uint64_t *hi,
                    void *stream);
@@ -436,7 +441,9 @@ typedef struct {
 
 /*
  * xm_count_stats -- xm_count_range with the counters above (a separately
- * compiled, slower kernel; for measurement, not for timing).
+ * compiled, slower kernel; for measurement, not for timing). Through a
+ * cut-vertex split the counters are summed over the instrumented passes of
+ * the parts and rooted quotients (load-balance times: the last pass's).
  */
 int xm_count_stats(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t *lo, uint64_t *hi,
                    xm_stats *stats, void *stream);
@@ -478,9 +485,11 @@ int xm_enumerate_roots(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroo
  * count twice. One launch for all nodes: the matcher adds each work unit's
  * count to a 128-bit device counter of its start node (Alg. 2 runs the
  * start nodes as independent tasks, so the per-node counts add up to
- * xm_count_roots). Uses the plan's leaf product, never the cut-vertex
- * decomposition. Device counters: 16 B per distinct root, allocated with the
- * graph on first use. Errors as xm_count_roots, XM_ENOMEM.
+ * xm_count_roots). Uses the plan's leaf product, and the cut-vertex
+ * decomposition where xm_count_range does (one launch per part and per
+ * rooted quotient, combined per node on the host). Device counters: 16 B per
+ * distinct root per launch, allocated with the graph on first use. Errors as
+ * xm_count_roots, XM_ENOMEM.
  */
 int xm_count_roots_each(xm_graph g, xm_plan p, const int32_t *roots, int64_t nroots, uint64_t *counts,
                         void *stream);
@@ -496,8 +505,11 @@ int xm_enumerate_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, 
 /*
  * xm_graph_last_timing -- device time of the last count/enumerate call on
  * this graph handle, from CUDA events recorded on the call's stream around
- * its kernels: *prep_ms covers the work-unit count and scan kernels,
- * *match_ms the persistent matcher kernel. Either pointer may be NULL.
+ * its kernels: *prep_ms covers the first-level, work-unit and scan kernels,
+ * *match_ms the persistent matcher kernel, each summed over the call's
+ * matching passes (one, or one per part and quotient of a cut-vertex split;
+ * the split's product kernel and host steps are not included). Either
+ * pointer may be NULL.
  * Errors: XM_EINVAL (no call yet), XM_ECUDA.
  */
 int xm_graph_last_timing(xm_graph g, float *prep_ms, float *match_ms);
@@ -557,11 +569,12 @@ int xm_batch_tune(xm_batch b, const xm_tuning *cand, int32_t ncand, int32_t reps
                   void *stream);
 
 /*
- * xm_batch_set_pair_budget -- a device-time budget for every pair of the
- * batch (0 = none; the default). A pair whose work has run this long since
- * its first work unit started (GPU global timer) stops: its remaining units
- * are skipped and xm_batch_pair_status reports XM_ETIMEOUT for it; its count
- * is incomplete. The other pairs finish exactly, and xm_batch_counts still
+ * xm_batch_set_pair_budget -- a device-time budget for every work unit of
+ * every pair of the batch (0 = none; the default). A work unit (one block of
+ * start nodes of one pair) that has run this long since it started (GPU
+ * global timer) stops, its pair's remaining units are skipped and
+ * xm_batch_pair_status reports XM_ETIMEOUT for the pair; its count is
+ * incomplete. Time a unit waits behind other pairs' units is not charged. The other pairs finish exactly, and xm_batch_counts still
  * returns XM_OK. The tuning's budget_ms, which ends the whole launch, stays
  * separate. Drops a captured CUDA graph (captured again on the next
  * xm_batch_run_graph).

@@ -196,7 +196,7 @@ class Graph:
 
         class _View:  # a device array by pointer, for torch.as_tensor
             def __init__(self, ptr, count):
-                self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<i4", "data": (ptr, True),
+                self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<i4", "data": (ptr, False),
                                                  "version": 3}
 
         oo, oa, io, ia = self.csr_pointers()

@@ -219,6 +219,7 @@ static int run_plan(xm_graph g, const Plan& P, const xm_tuning& t, int mode, int
     a.budget_ns = (unsigned long long)t.budget_ms * 1000000ull;
     a.root_counts = root_counts;
     a.merge_ratio = t.merge_ratio;
+  retry:
     XM_CUDA(cudaMemsetAsync(g->d_ctl, 0, CTL_WORDS * sizeof(unsigned long long), stream), "cudaMemsetAsync");
     XM_CUDA(cudaMemcpyAsync(ctl_plan(g), &P.dev, sizeof(XmPlanDev), cudaMemcpyHostToDevice, stream),
             "plan upload");
@@ -228,7 +229,21 @@ static int run_plan(xm_graph g, const Plan& P, const xm_tuning& t, int mode, int
     unsigned long long ctl[CTL_WORDS];
     XM_CUDA(cudaMemcpyAsync(ctl, g->d_ctl, sizeof ctl, cudaMemcpyDeviceToHost, stream), "result readback");
     XM_CUDA(cudaStreamSynchronize(stream), "matcher execution");
+    {
+        float a = 0.f, b = 0.f;
+        XM_CUDA(cudaEventElapsedTime(&a, g->ev[0], g->ev[1]), "cudaEventElapsedTime");
+        XM_CUDA(cudaEventElapsedTime(&b, g->ev[1], g->ev[2]), "cudaEventElapsedTime");
+        g->sum_prep_ms += a;
+        g->sum_match_ms += b;
+    }
     if (ctl[CTL_STATUS] & STATUS_TIMEOUT) { set_error("time budget of the matcher exceeded; no count"); return XM_ETIMEOUT; }
+    if ((ctl[CTL_STATUS] & STATUS_OVERFLOW) && a.unit <= (1 << 20)) {
+        // more work units than an int32 index space holds: the matcher
+        // walked nothing (the per-node counters are untouched); again with
+        // eight times larger units
+        a.unit *= 8;
+        goto retry;
+    }
     if (ctl[CTL_STATUS]) { set_error("work-unit count exceeds 2^31-1 (raise the unit size)"); return XM_EINVAL; }
     if (mode == MODE_EMIT) {
         *lo = ctl[CTL_EMIT];
@@ -261,6 +276,13 @@ static int run_plan(xm_graph g, const Plan& P, const xm_tuning& t, int mode, int
         return XM_EOVERFLOW;
     }
     return XM_OK;
+}
+
+// Start of a public call: its passes' event times are summed from zero.
+static void begin_call(xm_graph g) {
+    if (!g) return;
+    g->sum_prep_ms = 0.f;
+    g->sum_match_ms = 0.f;
 }
 
 static int run(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, int32_t* out, uint64_t capacity,
@@ -330,6 +352,90 @@ static int count_plan(xm_graph g, const Plan& P, const xm_tuning& t, u128& resul
         emb -= q * (u128)d->quots[j].aut_size * (u128)d->quot_mult[j];
     }
     result = (P.flags & XM_EMBEDDINGS) ? emb : emb / (u128)P.aut_size;
+    return XM_OK;
+}
+
+// Adds the counters of one pass to a running total (load-balance times: the
+// latest pass's).
+static void add_stats(xm_stats& acc, const xm_stats& s) {
+    acc.alg_bytes += s.alg_bytes;
+    acc.extensions += s.extensions;
+    acc.set_ops += s.set_ops;
+    acc.units += s.units;
+    acc.leaf_elems += s.leaf_elems;
+    acc.l1_bytes += s.l1_bytes;
+    acc.touched_bytes += s.touched_bytes;
+    acc.warp_exit_first_ns = s.warp_exit_first_ns;
+    acc.warp_exit_mean_ns = s.warp_exit_mean_ns;
+    acc.warp_exit_last_ns = s.warp_exit_last_ns;
+}
+
+// Whether counts of P over a subset of its start nodes go through its
+// cut-vertex decomposition (Decomp::rooted).
+static bool rooted_split(const Plan& P) { return P.decomp && P.decomp->rooted; }
+
+// Count (MODE_COUNT) or instrumented count (MODE_STATS, *stats summed over
+// the passes) of plan P over start nodes [r_lo, r_hi) or the staged root
+// list, through the cut-vertex decomposition rooted at the start vertex
+// (rooted_split(P)): per start-node part counts, their product sum (one
+// kernel), minus the rooted quotient counts over the same start nodes.
+static int count_split_sub(xm_graph g, const Plan& P, const xm_tuning& t, int mode, int64_t r_lo, int64_t r_hi,
+                           const int32_t* roots, int64_t nroots, u128& result, xm_stats* stats, cudaStream_t stream) {
+    const Decomp* d = P.decomp.get();
+    const int nparts = (int)d->parts.size();
+    const int64_t N = roots ? nroots : (int64_t)g->n;  // counter index space
+    const size_t words = (size_t)nparts * 2 * (size_t)N + 2;
+    int rc = ensure_root_counts(g, words);
+    if (rc) return rc;
+    unsigned long long* cnt = g->d_root_counts;
+    unsigned long long* sum = cnt + (size_t)nparts * 2 * N;
+    XM_CUDA(cudaMemsetAsync(cnt, 0, words * sizeof(unsigned long long), stream), "memset");
+    if (stats) memset(stats, 0, sizeof *stats);
+    xm_stats st{};
+    for (int i = 0; i < nparts; i++) {
+        uint64_t lo = 0, hi = 0;
+        // per-node counters need count mode; the stats pass of a part runs
+        // after it over the same start nodes
+        rc = run_plan(g, d->parts[i], t, MODE_COUNT, r_lo, r_hi, nullptr, 0, &lo, &hi, nullptr, nullptr, stream,
+                      roots, nroots, cnt + (size_t)i * 2 * N);
+        if (rc) return rc;
+        if (mode == MODE_STATS) {
+            rc = run_plan(g, d->parts[i], t, MODE_STATS, r_lo, r_hi, nullptr, 0, &lo, &hi, &st, nullptr, stream,
+                          roots, nroots);
+            if (rc) return rc;
+            add_stats(*stats, st);
+        }
+    }
+    cudaError_t e = launch_root_product(cnt, nparts, (int32_t)N, sum, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "part products");
+    unsigned long long s2[2];
+    XM_CUDA(cudaMemcpyAsync(s2, sum, sizeof s2, cudaMemcpyDeviceToHost, stream), "product readback");
+    XM_CUDA(cudaStreamSynchronize(stream), "part products");
+    u128 emb = (((u128)s2[1] << 64) | s2[0]) * (u128)d->part_factor;
+    for (size_t j = 0; j < d->rquots.size(); j++) {
+        uint64_t lo = 0, hi = 0;
+        rc = run_plan(g, d->rquots[j], t, mode, r_lo, r_hi, nullptr, 0, &lo, &hi, mode == MODE_STATS ? &st : nullptr,
+                      nullptr, stream, roots, nroots);
+        if (rc) return rc;
+        if (mode == MODE_STATS) add_stats(*stats, st);
+        const u128 q = ((u128)hi << 64) | lo;
+        emb -= q * (u128)d->rquots[j].stab_size * (u128)d->quot_mult[j];
+    }
+    result = (P.flags & XM_EMBEDDINGS) ? emb : emb / (u128)P.aut_size;
+    return XM_OK;
+}
+
+// Count or instrumented count of plan p over a start-node range or the staged
+// root list: the cut-vertex decomposition when it applies, else one pass.
+static int count_sub(xm_graph g, xm_plan p, int mode, int64_t r_lo, int64_t r_hi, const int32_t* roots,
+                     int64_t nroots, uint64_t* lo, uint64_t* hi, xm_stats* stats, cudaStream_t stream) {
+    if (!rooted_split(p->plan))
+        return run(g, p, mode, r_lo, r_hi, nullptr, 0, lo, hi, stats, nullptr, stream, roots, nroots);
+    u128 r = 0;
+    int rc = count_split_sub(g, p->plan, p->tuning, mode, r_lo, r_hi, roots, nroots, r, stats, stream);
+    if (rc) return rc;
+    *lo = (uint64_t)r;
+    *hi = (uint64_t)(r >> 64);
     return XM_OK;
 }
 
@@ -529,12 +635,10 @@ void xm_graph_free(xm_graph g) { free_graph(g); }
 
 int xm_graph_last_timing(xm_graph g, float* prep_ms, float* match_ms) {
     if (!g || !g->timed) { set_error("no timed call on this graph yet"); return XM_EINVAL; }
-    float a = 0, b = 0;
-    XM_CUDA(cudaEventSynchronize(g->ev[2]), "cudaEventSynchronize");
-    XM_CUDA(cudaEventElapsedTime(&a, g->ev[0], g->ev[1]), "cudaEventElapsedTime");
-    XM_CUDA(cudaEventElapsedTime(&b, g->ev[1], g->ev[2]), "cudaEventElapsedTime");
-    if (prep_ms) *prep_ms = a;
-    if (match_ms) *match_ms = b;
+    // every pass of the last call synchronised its stream before returning,
+    // so the sums are complete
+    if (prep_ms) *prep_ms = g->sum_prep_ms;
+    if (match_ms) *match_ms = g->sum_match_ms;
     return XM_OK;
 }
 
@@ -758,6 +862,7 @@ static int tune(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, con
 
 int xm_count(xm_graph g, xm_plan p, uint64_t* lo, uint64_t* hi, void* stream) {
     if (!g || !p || !lo || !hi) { set_error("NULL argument"); return XM_EINVAL; }
+    begin_call(g);
     u128 r = 0;
     int rc = count_plan(g, p->plan, p->tuning, r, (cudaStream_t)stream);
     if (rc) return rc;
@@ -768,13 +873,17 @@ int xm_count(xm_graph g, xm_plan p, uint64_t* lo, uint64_t* hi, void* stream) {
 
 int xm_count_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t* lo, uint64_t* hi,
                    void* stream) {
-    return run(g, p, MODE_COUNT, root_lo, root_hi, nullptr, 0, lo, hi, nullptr, nullptr, (cudaStream_t)stream);
+    if (!g || !p || !lo || !hi) { set_error("NULL argument"); return XM_EINVAL; }
+    begin_call(g);
+    return count_sub(g, p, MODE_COUNT, root_lo, root_hi, nullptr, 0, lo, hi, nullptr, (cudaStream_t)stream);
 }
 
 int xm_count_stats(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, uint64_t* lo, uint64_t* hi,
                    xm_stats* stats, void* stream) {
     if (!stats) { set_error("NULL stats"); return XM_EINVAL; }
-    return run(g, p, MODE_STATS, root_lo, root_hi, nullptr, 0, lo, hi, stats, nullptr, (cudaStream_t)stream);
+    if (!g || !p || !lo || !hi) { set_error("NULL argument"); return XM_EINVAL; }
+    begin_call(g);
+    return count_sub(g, p, MODE_STATS, root_lo, root_hi, nullptr, 0, lo, hi, stats, (cudaStream_t)stream);
 }
 
 // Uploads a validated, sorted, repeat-free copy of a host root list into the
@@ -810,8 +919,8 @@ int xm_count_roots(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, 
     int rc = stage_roots(g, roots, nroots, &kept, (cudaStream_t)stream);
     if (rc) return rc;
     if (kept == 0) { *lo = *hi = 0; return XM_OK; }
-    return run(g, p, MODE_COUNT, 0, INT32_MAX, nullptr, 0, lo, hi, nullptr, nullptr, (cudaStream_t)stream, g->d_roots,
-               kept);
+    begin_call(g);
+    return count_sub(g, p, MODE_COUNT, 0, INT32_MAX, g->d_roots, kept, lo, hi, nullptr, (cudaStream_t)stream);
 }
 
 int xm_count_roots_each(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, uint64_t* counts,
@@ -829,21 +938,49 @@ int xm_count_roots_each(xm_graph g, xm_plan p, const int32_t* roots, int64_t nro
     if (kept == 0) return XM_OK;
     int rc = stage_roots(g, r.data(), kept, nullptr, stream);
     if (rc) return rc;
-    if ((rc = ensure_root_counts(g, 2 * (size_t)kept))) return rc;
-    XM_CUDA(cudaMemsetAsync(g->d_root_counts, 0, 2 * (size_t)kept * sizeof(unsigned long long), stream), "memset");
-    uint64_t lo = 0, hi = 0;
-    rc = run_plan(g, p->plan, p->tuning, MODE_COUNT, 0, INT32_MAX, nullptr, 0, &lo, &hi, nullptr, nullptr, stream,
-                  g->d_roots, kept, g->d_root_counts);
-    if (rc) return rc;
-    std::vector<uint64_t> per(2 * (size_t)kept);
+    begin_call(g);
+    // one pass of the plan, or (rooted cut-vertex split) one pass per part
+    // and per rooted quotient, each with its own per-root counters
+    const Plan& P = p->plan;
+    const Decomp* d = rooted_split(P) ? P.decomp.get() : nullptr;
+    std::vector<const Plan*> passes;
+    if (d) {
+        for (const Plan& q : d->parts) passes.push_back(&q);
+        for (const Plan& q : d->rquots) passes.push_back(&q);
+    } else {
+        passes.push_back(&P);
+    }
+    const size_t per_pass = 2 * (size_t)kept;
+    if ((rc = ensure_root_counts(g, per_pass * passes.size()))) return rc;
+    XM_CUDA(cudaMemsetAsync(g->d_root_counts, 0, per_pass * passes.size() * sizeof(unsigned long long), stream),
+            "memset");
+    for (size_t i = 0; i < passes.size(); i++) {
+        uint64_t lo = 0, hi = 0;
+        rc = run_plan(g, *passes[i], p->tuning, MODE_COUNT, 0, INT32_MAX, nullptr, 0, &lo, &hi, nullptr, nullptr,
+                      stream, g->d_roots, kept, g->d_root_counts + i * per_pass);
+        if (rc) return rc;
+    }
+    std::vector<uint64_t> per(per_pass * passes.size());
     XM_CUDA(cudaMemcpyAsync(per.data(), g->d_root_counts, per.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost,
                             stream),
             "per-root readback");
     XM_CUDA(cudaStreamSynchronize(stream), "per-root readback");
+    auto at = [&](size_t pass, int64_t j) { return ((u128)per[pass * per_pass + 2 * j + 1] << 64) | per[pass * per_pass + 2 * j]; };
+    std::vector<u128> res((size_t)kept);
+    for (int64_t j = 0; j < kept; j++) {
+        if (!d) { res[j] = at(0, j); continue; }
+        // the per-node form of the split identity (Decomp::rooted)
+        const size_t np = d->parts.size();
+        u128 emb = (u128)d->part_factor;
+        for (size_t i = 0; i < np; i++) emb *= at(i, j);
+        for (size_t q = 0; q < d->rquots.size(); q++)
+            emb -= at(np + q, j) * (u128)d->rquots[q].stab_size * (u128)d->quot_mult[q];
+        res[j] = (P.flags & XM_EMBEDDINGS) ? emb : emb / (u128)P.aut_size;
+    }
     for (int64_t i = 0; i < nroots; i++) {
         const int64_t j = std::lower_bound(r.begin(), r.end(), roots[i]) - r.begin();
-        counts[2 * i] = per[2 * j];
-        counts[2 * i + 1] = per[2 * j + 1];
+        counts[2 * i] = (uint64_t)res[j];
+        counts[2 * i + 1] = (uint64_t)(res[j] >> 64);
     }
     return XM_OK;
 }
@@ -859,8 +996,8 @@ int xm_count_roots_stats(xm_graph g, xm_plan p, const int32_t* roots, int64_t nr
         memset(stats, 0, sizeof *stats);
         return XM_OK;
     }
-    return run(g, p, MODE_STATS, 0, INT32_MAX, nullptr, 0, lo, hi, stats, nullptr, (cudaStream_t)stream, g->d_roots,
-               kept);
+    begin_call(g);
+    return count_sub(g, p, MODE_STATS, 0, INT32_MAX, g->d_roots, kept, lo, hi, stats, (cudaStream_t)stream);
 }
 
 int xm_enumerate_roots(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroots, int32_t* dev_out,
@@ -870,6 +1007,7 @@ int xm_enumerate_roots(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroo
     int rc = stage_roots(g, roots, nroots, &kept, (cudaStream_t)stream);
     if (rc) return rc;
     if (kept == 0) { *total = *written = 0; return XM_OK; }
+    begin_call(g);
     uint64_t lo = 0, hi = 0, w = 0;
     rc = run(g, p, MODE_EMIT, 0, INT32_MAX, dev_out, capacity, &lo, &hi, nullptr, &w, (cudaStream_t)stream,
              g->d_roots, kept);
@@ -883,6 +1021,7 @@ int xm_enumerate_roots(xm_graph g, xm_plan p, const int32_t* roots, int64_t nroo
 int xm_enumerate_range(xm_graph g, xm_plan p, int64_t root_lo, int64_t root_hi, int32_t* dev_out,
                        uint64_t capacity, uint64_t* total, uint64_t* written, void* stream) {
     if (!total || !written) { set_error("NULL output"); return XM_EINVAL; }
+    begin_call(g);
     uint64_t lo = 0, hi = 0, w = 0;
     int rc = run(g, p, MODE_EMIT, root_lo, root_hi, dev_out, capacity, &lo, &hi, nullptr, &w, (cudaStream_t)stream);
     if (rc == XM_OK || rc == XM_EOVERFLOW) {

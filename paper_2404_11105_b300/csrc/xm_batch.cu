@@ -24,7 +24,7 @@ struct xm_batch_s {
     long long* d_prefix = nullptr;
     unsigned long long* d_counts = nullptr;
     unsigned long long* d_ctl = nullptr;
-    unsigned long long* d_pair_words = nullptr;  // per pair: start time, status (per-pair budgets)
+    unsigned long long* d_pair_words = nullptr;  // per pair: unused word, status (per-pair budgets)
     int32_t pair_budget_ms = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -84,7 +84,6 @@ BatchDev descriptor(const xm_batch_s* b) {
     d.budget_ns = (unsigned long long)b->tuning.budget_ms * 1000000ull;
     d.merge_ratio = b->tuning.merge_ratio;
     d.pair_budget_ns = (unsigned long long)b->pair_budget_ms * 1000000ull;
-    d.pair_t0 = b->d_pair_words;
     d.pair_status = b->d_pair_words + b->npairs;
     return d;
 }

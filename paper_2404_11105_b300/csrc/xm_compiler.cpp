@@ -412,7 +412,10 @@ constexpr int kMaxQuotientPartitions = 4096;
 // lowest id) and builds out.decomp: rooted plans of the parts and the
 // quotient patterns with their multiplicities. Leaves out.decomp null when
 // the pattern has no cut vertex or too many quotients.
-int decompose(const Pat& P, int flags, Plan& out, std::string& err) {
+// With `start_fixed` (every automorphism fixes the plan's start vertex) and
+// the cut vertex chosen equal to that start vertex, every quotient is also
+// compiled rooted at the cut vertex, for counts restricted to start nodes.
+int decompose(const Pat& P, int flags, Plan& out, std::string& err, bool start_fixed) {
     const int k = P.k;
     int cut = -1, best_big = 0;
     std::vector<uint32_t> best_parts;
@@ -431,6 +434,7 @@ int decompose(const Pat& P, int flags, Plan& out, std::string& err) {
     const int sub_flags = flags & (XM_NO_REDUCE | XM_NO_PRODUCT | XM_NO_SPLIT);
     auto d = std::make_shared<Decomp>();
     d->cut = cut;
+    d->rooted = start_fixed && cut == out.start;
     int part_of[XM_MAXK];
     for (int v = 0; v < k; v++) part_of[v] = -1;
     for (size_t i = 0; i < best_parts.size(); i++) {
@@ -486,6 +490,14 @@ int decompose(const Pat& P, int flags, Plan& out, std::string& err) {
         Plan q;
         int rc = compile_pattern(qk, (int)s.size(), s.data(), t.data(), sub_flags, q, err);
         if (rc) return rc;
+        if (d->rooted) {
+            // the quotient rooted at the cut vertex (label 0): its rooted
+            // matches at node v times |Stab(0)| are its embeddings mapping c to v
+            Plan qr;
+            rc = compile_pattern(qk, (int)s.size(), s.data(), t.data(), sub_flags | XM_NO_SPLIT, qr, err, 0);
+            if (rc) return rc;
+            d->rquots.push_back(std::move(qr));
+        }
         keys.push_back(key);
         d->quots.push_back(std::move(q));
         d->quot_mult.push_back(1);
@@ -812,7 +824,10 @@ int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pd
     // Counting by a cut vertex, when the plan still walks three or more
     // levels (a product at level 2 is cheaper than any split).
     if (root < 0 && k >= 4 && !(flags & (XM_INDUCED | XM_NO_SPLIT)) && (D.prod_r == 0 || D.prod_p >= 3)) {
-        int rc = decompose(P, flags, out, err);
+        bool start_fixed = true;
+        for (auto& g : aut)
+            if (g[out.start] != out.start) start_fixed = false;
+        int rc = decompose(P, flags, out, err, start_fixed);
         if (rc) return rc;
     }
     return XM_OK;
@@ -871,6 +886,12 @@ std::string describe_plan(const Plan& p) {
                      V.hi_mask, V.neq_mask);
             s += buf;
         }
+    }
+    if (p.decomp) {
+        snprintf(buf, sizeof buf, "cut-vertex split: cut %d, %d parts, %d quotients, start-node subsets %s\n",
+                 p.decomp->cut, (int)p.decomp->parts.size(), (int)p.decomp->quots.size(),
+                 p.decomp->rooted ? "split" : "walked");
+        s += buf;
     }
     return s;
 }

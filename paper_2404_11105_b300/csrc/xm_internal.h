@@ -46,6 +46,15 @@ struct Decomp {
     long long part_factor = 1;   // prod_i |Stab(c) in Aut(A_i + c)|: rooted matches -> embeddings
     std::vector<Plan> quots;     // the quotients P/s, one per isomorphism class
     std::vector<long long> quot_mult;  // number of partitions s in each class
+    // Counts restricted to start nodes. When the cut vertex is the plan's
+    // start vertex and every automorphism fixes it, all embeddings of one
+    // match map c to the same node, and for any node set R
+    //   emb_R(P) = part_factor * sum_{v in R} prod_i m_i(v)
+    //              - sum_j mult_j * |Stab_j(c)| * sum_{v in R} r_j(v),
+    // r_j(v) the rooted matches of quotient j with c mapped to v: rquots[j],
+    // Q_j compiled rooted at c (its label 0).
+    bool rooted = false;
+    std::vector<Plan> rquots;
 };
 
 int compile_pattern(int32_t k, int32_t e, const int32_t* psrc, const int32_t* pdst, int flags, Plan& out,
@@ -109,7 +118,10 @@ struct xm_graph_s {
     unsigned long long* d_ctl = nullptr;
     int64_t n_block_sums = 0;
     int64_t cmax = 0;
-    // events around the last call's kernels (prep start, match start, match end)
+    // events around the last matching pass's kernels (prep start, match
+    // start, match end), and the sums of those times over the passes of the
+    // last public call (several for a cut-vertex split)
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     bool timed = false;
+    float sum_prep_ms = 0.f, sum_match_ms = 0.f;
 };

@@ -67,6 +67,15 @@ struct Budget {
         }
         deadline = __shfl_sync(FULL, t0, 0) + budget_ns;
     }
+    // A budget of one work unit: the deadline counts from this warp's start
+    // of the unit; `st` is shared by all units of the same work (one pair).
+    __device__ void start_unit(unsigned long long* st, unsigned long long budget_ns, int lane) {
+        status = st;
+        deadline = 0;
+        if (!budget_ns) return;
+        const unsigned long long now = lane == 0 ? global_ns() : 0ull;
+        deadline = __shfl_sync(FULL, now, 0) + budget_ns;
+    }
     // true when the work must stop (warp-uniform)
     __device__ bool expired(int lane) const {
         if (!deadline) return false;
@@ -1652,6 +1661,9 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
     // of a first-level candidate's second-level driver range
     const int32_t* uprefix = two_level ? ra.units : ra.e_units;
     const int nidx = two_level ? ra.n_idx : ra.emax;
+    // a work-unit scan that overflowed int32 left wrapped prefixes: walk
+    // nothing (the host sees the status bit and retries with larger units)
+    if (*((volatile unsigned long long*)(ra.ctl + CTL_STATUS)) & STATUS_OVERFLOW) return;
     const int total = uprefix[nidx];
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     // walks of four or more levels: the units of one heavy start node lie
@@ -1892,11 +1904,15 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
                     reinterpret_cast<int32_t*>(&P)[i] = reinterpret_cast<const int32_t*>(b.plans + pg.x)[i];
                 g = b.graphs[pg.y];
                 __syncwarp();
-                if (b.pair_budget_ns)
-                    pair_budget.start_at(b.pair_t0 + cur, b.pair_status + cur, b.pair_budget_ns, lane);
             }
-            // a pair over its own budget: its remaining units are skipped
-            if (b.pair_budget_ns && pair_budget.expired(lane)) continue;
+            // per-pair budgets count from the start of each unit, so that time a
+            // pair's units spend queued behind other pairs' units in a warp's
+            // grab is not charged to it; once one unit of a pair runs out, the
+            // pair's remaining units are skipped
+            if (b.pair_budget_ns) {
+                pair_budget.start_unit(b.pair_status + cur, b.pair_budget_ns, lane);
+                if (pair_budget.expired(lane)) continue;
+            }
             const int r0 = (int)(u - __ldg(b.unit_prefix + cur)) * b.root_block;
             const int r1 = min(r0 + b.root_block, g.n);
             const int k = P.k;

@@ -135,8 +135,7 @@ struct BatchDev {
     unsigned long long budget_ns;    // time budget (0: none)
     int32_t kmax;                    // largest pattern in the batch
     int32_t merge_ratio;             // as RunArgs::merge_ratio
-    unsigned long long pair_budget_ns = 0;  // per-pair budget (0: none)
-    unsigned long long* pair_t0 = nullptr;      // per pair: global timer when its first unit started
+    unsigned long long pair_budget_ns = 0;  // per-pair budget of each work unit (0: none)
     unsigned long long* pair_status = nullptr;  // per pair: STATUS_TIMEOUT when its budget ran out
 };
 

@@ -308,6 +308,34 @@ def test_split_choices():
         assert xm.Plan(synth.FFCHAIN5, flags).split()["cut"] == -1
 
 
+SUBSET_SPLIT = dict(SPLIT_PATTERNS, **{
+    # the cut vertex is the start vertex but an automorphism moves it
+    "sym2": (6, [(0, 1), (1, 0), (0, 2), (2, 3), (1, 4), (4, 5)]),
+    "twotri": (6, [(0, 1), (1, 0), (0, 2), (2, 3), (3, 0), (1, 4), (4, 5), (5, 1)]),
+    "sym3": (7, [(0, 1), (1, 0), (0, 2), (2, 3), (3, 0), (1, 4), (4, 5), (5, 1), (6, 0)]),
+})
+
+
+@pytest.mark.parametrize("name", sorted(SUBSET_SPLIT))
+def test_split_over_start_node_subsets_choice(name):
+    """Counts over a start-node range or list use the decomposition exactly
+    when the cut vertex is the plan's start vertex and every automorphism
+    (the oracle's, by brute force) fixes it: then all embeddings of a match
+    send the cut vertex to one node, and per-node sums are exact."""
+    pattern = SUBSET_SPLIT[name]
+    plan = xm.Plan(pattern)
+    sp = plan.split()
+    if sp["cut"] < 0:
+        return
+    fixed = all(row[sp["cut"]] == sp["cut"] for row in oracle.automorphisms(pattern))
+    want = "split" if (sp["cut"] == plan.start and fixed) else "walked"
+    line = [ln for ln in plan.describe().splitlines() if ln.startswith("cut-vertex split:")]
+    assert line and line[0].endswith("start-node subsets " + want), (name, line)
+    for name2, w in (("ffchain5", "split"), ("bowtie", "split"), ("sym2", "walked"), ("path5", "walked")):
+        if name == name2:
+            assert want == w
+
+
 @pytest.mark.parametrize("seed", [7, 8])
 @pytest.mark.parametrize("name", sorted(SPLIT_PATTERNS))
 def test_split_identity_vs_oracle(seed, name):

@@ -614,6 +614,43 @@ def test_split_counts_eight_vertices(xm, name):
     assert xm.xm_count(g, xm.Plan(pat, xm.XM_EMBEDDINGS)) == og.count_embeddings(pat)
 
 
+@pytest.mark.parametrize("name", ["ffchain5", "tri_tail", "bowtie", "path5"])
+def test_split_over_start_node_subsets(xm, rmat_small, name):
+    """Counts over start-node ranges and lists through the cut-vertex split
+    rooted at the start vertex (part counts per start node, their product
+    sum, rooted quotients) equal the whole-pattern walk over the same start
+    nodes and the oracle rooted at the start vertex; ranges that partition
+    the nodes add up to xm_count; the instrumented count agrees; a pattern
+    whose cut vertex is not its start vertex (path5) is walked."""
+    g, og = rmat_small
+    pat = SPLIT_PATTERNS[name]
+    p, walk = xm.Plan(pat), xm.Plan(pat, xm.XM_NO_SPLIT)
+    pe, walk_e = xm.Plan(pat, xm.XM_EMBEDDINGS), xm.Plan(pat, xm.XM_EMBEDDINGS | xm.XM_NO_SPLIT)
+    assert p.split()["cut"] >= 0
+    cuts = [0, 1, 3, 64, 500, 900, g.n]
+    per = [xm.xm_count_range(g, p, a, b) for a, b in zip(cuts, cuts[1:])]
+    assert per == [xm.xm_count_range(g, walk, a, b) for a, b in zip(cuts, cuts[1:])]
+    assert sum(per) == xm.xm_count(g, p) == og.count_matches(pat)
+    prep, match = g.last_timing()
+    assert prep >= 0 and match > 0
+    rng = np.random.default_rng(11)
+    # the hubs of the skewed graph and a seeded uniform sample
+    off, adj = og.out_csr()
+    deg = np.diff(off) + np.bincount(adj, minlength=g.n)
+    roots = np.concatenate([np.argsort(-deg)[:6], rng.integers(0, g.n, 30)]).astype(np.int32)
+    want = [og.count_embeddings(pat, pe.start, v, v + 1) for v in roots.tolist()]
+    assert xm.xm_count_roots_each(g, pe, roots) == want
+    assert xm.xm_count_roots_each(g, walk_e, roots) == want
+    uniq = np.unique(roots)
+    c = xm.xm_count_roots(g, p, uniq)
+    assert c == xm.xm_count_roots(g, walk, uniq) == sum(xm.xm_count_roots_each(g, p, uniq))
+    assert xm.xm_count_roots(g, pe, uniq) == sum(og.count_embeddings(pat, pe.start, v, v + 1) for v in uniq.tolist())
+    cs, st = xm.xm_count_roots_stats(g, p, uniq)
+    assert cs == c and st["alg_bytes"] > 0
+    cs, st = xm.xm_count_stats(g, p, 64, 500)
+    assert cs == per[3] and st["alg_bytes"] > 0
+
+
 @pytest.mark.parametrize("name", sorted(SPLIT_PATTERNS))
 def test_split_counts(xm, tiny, rmat_tiny, name):
     """xm_count through the cut-vertex decomposition (per-node part counts,
