@@ -1631,7 +1631,12 @@ __device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDe
 // registers a thread, 48 warps an SM) for three-level plans, whose probe
 // loops are latency-bound and want warps; 2 (64 registers) for deeper
 // plans, whose batched last level needs the registers.
-template <int MODE, bool PROD, int MINB = 2>
+// Resident blocks of 512 threads the matcher's register budget is cut for
+// (2: 64 registers per thread).
+#ifndef XM_MATCH_MINB
+#define XM_MATCH_MINB 2
+#endif
+template <int MODE, bool PROD, int MINB = XM_MATCH_MINB>
 __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     // the three-level build leaves out the batched last level and the
     // merges (their registers would spill into its probe loops)
