@@ -393,8 +393,9 @@ std::vector<uint32_t> parts_without(const Pat& P, int c) {
 }
 
 // Isomorphism-invariant key of a pattern on k <= 8 vertices: the smallest
-// 64-bit adjacency matrix over all relabellings.
-uint64_t canonical_key(int k, const std::vector<std::pair<int, int>>& arcs) {
+// 64-bit adjacency matrix over all relabellings (with fix0, over the
+// relabellings that keep vertex 0: a key of the pattern rooted at 0).
+uint64_t canonical_key(int k, const std::vector<std::pair<int, int>>& arcs, bool fix0 = false) {
     std::vector<int> p(k);
     for (int i = 0; i < k; i++) p[i] = i;
     uint64_t best = ~0ull;
@@ -402,7 +403,7 @@ uint64_t canonical_key(int k, const std::vector<std::pair<int, int>>& arcs) {
         uint64_t key = 0;
         for (auto& a : arcs) key |= 1ull << (p[a.first] * 8 + p[a.second]);
         best = std::min(best, key);
-    } while (std::next_permutation(p.begin(), p.end()));
+    } while (std::next_permutation(p.begin() + (fix0 ? 1 : 0), p.end()));
     return best;
 }
 
@@ -482,7 +483,10 @@ int decompose(const Pat& P, int flags, Plan& out, std::string& err, bool start_f
             seen |= 1ull << (u * 8 + v);
             arcs.push_back({u, v});
         }
-        const uint64_t key = canonical_key(qk, arcs);
+        // counts rooted at the cut vertex (label 0) group only quotients that
+        // are isomorphic by a map keeping the cut vertex: two quotients
+        // isomorphic by a map that moves it have different rooted counts
+        const uint64_t key = canonical_key(qk, arcs, d->rooted);
         for (size_t j = 0; j < keys.size(); j++)
             if (keys[j] == key && d->quots[j].k == qk) { d->quot_mult[j]++; return XM_OK; }
         std::vector<int32_t> s, t;

@@ -121,9 +121,27 @@ struct LvState {
 // Per-warp state in shared memory. Only the first k entries of st[] exist
 // (the layout is cut to the plan's size so that more of the SM's on-chip
 // memory stays L1 cache); never index st[] at or beyond k.
+// Probes each lane keeps in flight in the batched last level.
+#ifndef XM_LEAF_PPL
+#define XM_LEAF_PPL 4
+#endif
+
+// One pair of a batched last level: its driver ids at d[t] for flattened
+// positions t < end (d is offset by the pair's first position), and the list
+// it probes (a hash table of n > 0 slots, or -n ascending ids).
+struct LeafPair {
+    const int32_t* d;
+    const int32_t* tab;
+    int32_t end;
+    int32_t n;
+};
+
 struct WarpSmem {
     int32_t* mtile;  // this warp's MERGE_TILE-id tile for merge intersections
     int32_t m[XM_MAXK];
+#if XM_LEAF_TABLE
+    LeafPair lp[32];  // the batched last level's pairs
+#endif
     LvState st[XM_MAXK];
 };
 
@@ -167,6 +185,29 @@ __device__ __forceinline__ int32_t ld(const int32_t* p, int i, bool shared) {
 
 // first index in [lo, hi) with p[idx] >= x
 __device__ __forceinline__ int lbound(const int32_t* p, int lo, int hi, int32_t x, bool shared) {
+#if XM_LB8
+    if (!shared) {
+        // eight-way search in global memory: each round reads seven evenly
+        // spaced ids at once (independent loads) and keeps the eighth of the
+        // range that must hold the answer, so a list of L ids costs about
+        // log8(L) dependent rounds instead of log2(L); the last <= 8 ids are
+        // read together and counted
+        while (hi - lo > 8) {
+            const int r = hi - lo;
+            int c = 0;
+#pragma unroll
+            for (int j = 1; j < 8; j++) c += __ldg(p + lo + (int)(((long long)r * j) >> 3)) < x ? 1 : 0;
+            const int nlo = c ? lo + (int)(((long long)r * c) >> 3) + 1 : lo;
+            const int nhi = c < 7 ? lo + (int)(((long long)r * (c + 1)) >> 3) : hi;
+            lo = nlo;
+            hi = nhi;
+        }
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) c += (lo + j < hi && __ldg(p + lo + j) < x) ? 1 : 0;
+        return lo + c;
+    }
+#endif
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
         if (ld(p, mid, shared) < x) lo = mid + 1; else hi = mid;
@@ -650,9 +691,8 @@ __device__ void setup_lists(const XmLevel& L, const GraphDev& g, WarpSmem& ws, L
                             bool whole) {
     int32_t lo, hi;
     level_bounds(L, ws.m, lo, hi);
-    ListRef lists[XM_MAXOPS + 1];
-    int cnt = 0;
-    // lane i fetches operand i's list bounds and hash table, all in parallel
+    // lane i fetches operand i's list bounds and hash table, all in parallel;
+    // the level's lists stay spread over the lanes (no per-thread array)
     ListRef mine{nullptr, 0, 0, nullptr, 0};
     if (lane < L.nops) mine = op_list(g, L.op_dir[lane], ws.m[L.op_level[lane]]);
     bool use_reuse = (L.reuse >= 1) && ws.st[L.reuse].complete;
@@ -662,48 +702,55 @@ __device__ void setup_lists(const XmLevel& L, const GraphDev& g, WarpSmem& ws, L
         const int len_i = __shfl_sync(FULL, mine.len, __ffs(L.reuse_ops) - 1);
         if (len_i == ws.st[L.reuse].set_len) use_reuse = false;
     }
-    if (use_reuse) {
-        const LvState& R = ws.st[L.reuse];
-        lists[cnt++] = {R.set_ptr, R.set_len, R.set_shared, nullptr, 0};
+    // entries in order: the reused set (when used), then the operands it does
+    // not cover; the driver is the first shortest entry
+    const LvState& R = ws.st[use_reuse ? L.reuse : 0];
+    const bool act = lane < L.nops && !(use_reuse && ((L.reuse_ops >> lane) & 1u));
+    const unsigned amask = __ballot_sync(FULL, act);
+    long long key = act ? (((long long)mine.len << 6) | (lane + 1)) : LLONG_MAX;
+    for (int o = 16; o; o >>= 1) key = min(key, __shfl_xor_sync(FULL, key, o));
+    if (use_reuse) key = min(key, (long long)R.set_len << 6);
+    const int dord = (int)(key & 63);  // 0: the reused set; i + 1: operand i
+    const int dlane = dord > 0 ? dord - 1 : 0;
+    bool empty = __any_sync(FULL, act && mine.len == 0) || (use_reuse && R.set_len == 0);
+    ListRef drv;
+    drv.p = reinterpret_cast<const int32_t*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.p), dlane));
+    drv.len = __shfl_sync(FULL, mine.len, dlane);
+    drv.shared = 0;
+    if (dord == 0) {
+        drv.p = R.set_ptr;
+        drv.len = R.set_len;
+        drv.shared = R.set_shared;
     }
-    for (int i = 0; i < L.nops; i++) {
-        ListRef r;
-        r.p = reinterpret_cast<const int32_t*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.p), i));
-        r.len = __shfl_sync(FULL, mine.len, i);
-        r.shared = 0;
-        r.tab = reinterpret_cast<const int32_t*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(mine.tab), i));
-        r.T = __shfl_sync(FULL, mine.T, i);
-        if (use_reuse && ((L.reuse_ops >> i) & 1u)) continue;
-        lists[cnt++] = r;
-    }
-    int d = 0;
-    bool empty = false;
-    for (int i = 0; i < cnt; i++) {
-        if (lists[i].len == 0) empty = true;
-        if (lists[i].len < lists[d].len) d = i;
-    }
-    int c0 = 0, c1 = lists[d].len;
+    int c0 = 0, c1 = drv.len;
     if (!empty) {
-        if (lo >= 0) c0 = lbound(lists[d].p, 0, c1, lo + 1, lists[d].shared);
-        if (hi != INT_MAX) c1 = lbound(lists[d].p, c0, c1, hi, lists[d].shared);
+        if (lo >= 0) c0 = lbound(drv.p, 0, c1, lo + 1, drv.shared);
+        if (hi != INT_MAX) c1 = lbound(drv.p, c0, c1, hi, drv.shared);
     }
     if (c0 >= c1) empty = true;
+    // probes: the other entries, in order
+    const bool reuse_probe = use_reuse && dord != 0;
+    const unsigned pmask = amask & ~(dord > 0 ? 1u << dlane : 0u);
+    if (act && !(dord > 0 && lane == dlane)) {
+        const int np = (reuse_probe ? 1 : 0) + __popc(pmask & ((1u << lane) - 1u));
+        S.probe[np] = mine.p;
+        S.ptab[np] = mine.tab;
+        S.pT[np] = mine.T;
+        S.plo[np] = 0;
+        S.phi[np] = mine.len;
+    }
     if (lane == 0) {
-        S.drv = lists[d].p;
-        S.drv_shared = lists[d].shared;
-        int np = 0, psh = 0;
-        for (int i = 0; i < cnt; i++) {
-            if (i == d) continue;
-            S.probe[np] = lists[i].p;
-            S.ptab[np] = lists[i].tab;
-            S.pT[np] = lists[i].T;
-            S.plo[np] = 0;
-            S.phi[np] = lists[i].len;
-            if (lists[i].shared) psh |= 1 << np;
-            np++;
+        if (reuse_probe) {
+            S.probe[0] = R.set_ptr;
+            S.ptab[0] = nullptr;
+            S.pT[0] = 0;
+            S.plo[0] = 0;
+            S.phi[0] = R.set_len;
         }
-        S.nprobe = np;
-        S.probe_shared = psh;
+        S.drv = drv.p;
+        S.drv_shared = drv.shared;
+        S.nprobe = (reuse_probe ? 1 : 0) + __popc(pmask);
+        S.probe_shared = reuse_probe && R.set_shared ? 1 : 0;
         S.c0 = c0;
         S.c1 = empty ? c0 : c1;
         S.drv_pos = c0;
@@ -712,15 +759,15 @@ __device__ void setup_lists(const XmLevel& L, const GraphDev& g, WarpSmem& ws, L
         S.complete = 0;
         S.wcnt = S.wpos = S.it_hi = 0;
         if (MODE == MODE_STATS) {
-            for (int i = 0; i < cnt; i++) {
-                if (lists[i].shared) continue;
-                st.bytes += 8;
-                st.touched += 32;
-            }
-            if (!lists[d].shared && lists[d].len > 0) {
+            // offsets of every list entry (a shared set costs none), and the
+            // driver's bound searches
+            const int nlist = __popc(amask) + (use_reuse && !R.set_shared ? 1 : 0);
+            st.bytes += 8ull * nlist;
+            st.touched += 32ull * nlist;
+            if (!drv.shared && drv.len > 0) {
                 const int nsearch = (lo >= 0 ? 1 : 0) + (hi != INT_MAX ? 1 : 0);
-                st.bytes += nsearch * search_bytes(lists[d].len);
-                st.touched += 32ull * nsearch * search_sectors(lists[d].len);
+                st.bytes += nsearch * search_bytes(drv.len);
+                st.touched += 32ull * nsearch * search_sectors(drv.len);
             }
         }
     }
@@ -1069,6 +1116,55 @@ __device__ unsigned long long leaf_batch(const XmPlanDev& P, const GraphDev& g, 
         ptab = F.T ? F.tab : F.p + a0;
         ptn = F.T ? (int)F.T : -na;
     }
+#if XM_LEAF_TABLE
+    // Each lane walks the flattened positions lane, lane + 32, ... and keeps
+    // the index of the pair its position falls in (pairs only ever advance),
+    // reading a pair's pointers from the warp's shared table when it moves
+    // on: no shuffles per probe.
+    constexpr int PPL = XM_LEAF_PPL;
+    ws.lp[lane] = LeafPair{dptr - pre, ptab, pend, ptn};
+    __syncwarp();
+    int pi = 0, pe = ws.lp[0].end;
+    for (int t0 = 0; t0 < total; t0 += 32 * PPL) {
+        int32_t x[PPL];
+        int q[PPL];
+#pragma unroll
+        for (int u = 0; u < PPL; u++) {
+            const int t = t0 + 32 * u + lane;
+            x[u] = -1;
+            q[u] = -1;
+            if (t < total) {
+                while (pe <= t) pe = ws.lp[++pi].end;
+                q[u] = pi;
+                x[u] = __ldg(ws.lp[pi].d + t);
+            }
+        }
+        bool f[PPL], dn[PPL];
+#pragma unroll
+        for (int u = 0; u < PPL; u++) {
+            f[u] = false;
+            dn[u] = true;
+            if (q[u] >= 0) {
+                const int32_t* tab = ws.lp[q[u]].tab;
+                const int n = ws.lp[q[u]].n;
+                if (n > 0) {
+                    dn[u] = hash_first(tab, (uint32_t)n, x[u], f[u]);
+                } else {
+                    const int r0 = lbound(tab, 0, -n, x[u], false);
+                    f[u] = r0 < -n && __ldg(tab + r0) == x[u];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PPL; u++) {
+            if (!dn[u]) f[u] = hash_has(ws.lp[q[u]].tab, (uint32_t)ws.lp[q[u]].n, x[u]);
+            for (uint32_t nm = neq; nm && f[u]; nm &= nm - 1) f[u] = x[u] != ws.m[__ffs(nm) - 1];
+            cnt += f[u] ? 1 : 0;
+        }
+    }
+    __syncwarp();
+    return cnt;
+#endif
     for (int t0 = 0; t0 < total; t0 += 128) {
         int32_t x[4];
         bool ok[4];
@@ -1112,6 +1208,40 @@ __device__ unsigned long long leaf_batch(const XmPlanDev& P, const GraphDev& g, 
     }
     return cnt;
 }
+
+#if XM_B4
+// The walk below a four-level plan's second level when its last level is a
+// batched two-list level (explore's behaviour for that shape, without the
+// deeper-level and other leaf paths): refill level 2's window from its
+// driver range, count each batch of up to 32 candidates with leaf_batch.
+template <int MODE>
+__device__ bool walk_last2(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int32_t* win, int W, int iF,
+                           int lane, const RunArgs& ra, unsigned long long& acc, Stats& st, const Budget& budget) {
+    LvState& S = ws.st[2];
+    unsigned steps = 0;
+    for (;;) {
+        if ((++steps & 255u) == 0 && budget.expired(lane)) return false;
+        if (S.wpos >= S.it_hi) {
+            if (S.complete || S.drv_pos >= S.drv_end) return true;
+            if (lane == 0) { S.wcnt = 0; S.wpos = 0; }
+            __syncwarp();
+            scan_level<MODE, true>(P, P.lv[2], g, ws, S, 2, win, W, lane, ra, st);
+            if (lane == 0) S.it_hi = S.wcnt;
+            __syncwarp();
+            continue;
+        }
+        const int nb = min(32, S.it_hi - S.wpos);
+        acc += leaf_batch<MODE>(P, g, ws, iF, S.it_ptr + S.wpos, S.it_shared, nb, lane, ra, st);
+        if (MODE == MODE_STATS && lane == 0) {
+            st.ext += nb;
+            st.sets += nb;
+        }
+        __syncwarp();
+        if (lane == 0) S.wpos += nb;
+        __syncwarp();
+    }
+}
+#endif
 
 // Adds a 128-bit value on lane 0 to the lane's running count, or straight to
 // the 128-bit counter when the 64-bit count would wrap.
@@ -1636,7 +1766,7 @@ __device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDe
 #ifndef XM_MATCH_MINB
 #define XM_MATCH_MINB 2
 #endif
-template <int MODE, bool PROD, int MINB = XM_MATCH_MINB>
+template <int MODE, bool PROD, int MINB = XM_MATCH_MINB, bool B4 = false>
 __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     // the three-level build leaves out the batched last level and the
     // merges (their registers would spill into its probe loops)
@@ -1661,7 +1791,9 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
     if (lane == 0) ws.mtile = tile ? wins + (size_t)n_windows(k) * W : nullptr;
     __syncwarp();
     const GraphDev& g = ra.g;
-    const bool two_level = !ra.l2_units;
+    // B4: four-level plans counted through units below the first level, whose
+    // last level is a batched two-list level (the launch checks the shape)
+    const bool two_level = B4 ? false : !ra.l2_units;
     // unit index space: pieces of a start node's first-level set, or pieces
     // of a first-level candidate's second-level driver range
     const int32_t* uprefix = two_level ? ra.units : ra.e_units;
@@ -1714,7 +1846,7 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
                 }
             }
             if (MODE == MODE_STATS && lane == 0) st.units++;
-            if (two_level && ke > 2) {
+            if (!B4 && two_level && ke > 2) {
                 // unit = (start node, a piece of its first-level set)
                 const int root = owner;
                 const int s0 = set_start(ra, root), s1 = set_start(ra, root + 1);
@@ -1748,7 +1880,7 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
                     stop = true;
                 continue;
             }
-            if (two_level) {
+            if (!B4 && two_level) {
                 // the first level is the last: every candidate is a match
                 const int root = owner;
                 const int s0 = set_start(ra, root), s1 = set_start(ra, root + 1);
@@ -1782,7 +1914,7 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
                 st.bytes += 4;
                 st.touched += 4;
             }
-            if (MODE != MODE_EMIT && ke == 3 &&
+            if (!B4 && MODE != MODE_EMIT && ke == 3 &&
                 leaf3_direct<MODE, LEAN>(P, g, root_node(ra, root), __ldg(ra.l1set + e), ra.l1set + s0, s1 - s0,
                                    chunk * per2, per2, lane, acc, ra, ws, st))
                 continue;
@@ -1799,7 +1931,7 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
             }
             __syncwarp();
             if (MODE == MODE_STATS && lane == 0) st.ext++;
-            if (ke == 3) {
+            if (!B4 && ke == 3) {
                 acc += leaf_level<MODE, LEAN>(P, g, ws, 2, lane, ra, st, chunk * per2, per2);
                 if (MODE == MODE_STATS && lane == 0) st.sets++;
                 continue;
@@ -1831,6 +1963,13 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
                 S2.set_shared = 1;
             }
             __syncwarp();
+#if XM_B4
+            if (B4) {
+                if (!walk_last2<MODE>(P, g, ws, win, W, batch_leaf_fixed_op(P), lane, ra, acc, st, budget))
+                    stop = true;
+                continue;
+            }
+#endif
             if (!explore<MODE, PROD, LEAN>(P, g, ws, wins, W, 2, lane, ra, acc, counter, st, budget, 2)) stop = true;
         }
         if (stop) break;
@@ -2187,12 +2326,18 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
     // three-level counts (the last level probed from registers) run the
     // 40-register build, which never merges
     const bool three = mode == MODE_COUNT && !prod && P.k == 3;
+#if XM_B4
+    const bool b4 = mode == MODE_COUNT && !prod && P.k == 4 && b.l2_units && batch_leaf_fixed_op(P) >= 0;
+#else
+    const bool b4 = false;
+#endif
     const size_t smem = match_smem_bytes(P.k, b.window, warps_per_block, b.merge_ratio > 0 && !three);
     const void* fn = mode == MODE_STATS  ? (prod ? (const void*)k_match<MODE_STATS, true>
                                                  : (const void*)k_match<MODE_STATS, false>)
                      : mode == MODE_EMIT ? (const void*)k_match<MODE_EMIT, false>
                      : prod              ? (const void*)k_match<MODE_COUNT, true>
                      : three             ? (const void*)k_match<MODE_COUNT, false, 3>
+                     : b4                ? (const void*)k_match<MODE_COUNT, false, XM_MATCH_MINB, true>
                                          : (const void*)k_match<MODE_COUNT, false>;
     if ((err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return err;
@@ -2213,6 +2358,10 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
         k_match<MODE_COUNT, true><<<grid, block, smem, stream>>>(plan_dev, b);
     else if (three)
         k_match<MODE_COUNT, false, 3><<<grid, block, smem, stream>>>(plan_dev, b);
+#if XM_B4
+    else if (b4)
+        k_match<MODE_COUNT, false, XM_MATCH_MINB, true><<<grid, block, smem, stream>>>(plan_dev, b);
+#endif
     else
         k_match<MODE_COUNT, false><<<grid, block, smem, stream>>>(plan_dev, b);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -380,3 +380,15 @@ def test_split_identity_vs_oracle(seed, name):
             assert q["pattern"][0] < k and q["mult"] >= 1
             total -= q["mult"] * g.count_embeddings(q["pattern"])
         assert total == g.count_embeddings(pattern)
+        if "start-node subsets split" in plan.describe():
+            # node by node: the embeddings mapping the cut vertex to v are the
+            # parts' products at v minus the quotients' embeddings rooted at v
+            # (the cut vertex is label 0 of every quotient)
+            assert plan.start == cut
+            for v in range(n):
+                per = 1
+                for part in sp["parts"]:
+                    per *= g.count_embeddings(part["pattern"], 0, v, v + 1)
+                for q in sp["quotients"]:
+                    per -= q["mult"] * g.count_embeddings(q["pattern"], 0, v, v + 1)
+                assert per == g.count_embeddings(pattern, cut, v, v + 1), (name, v)
