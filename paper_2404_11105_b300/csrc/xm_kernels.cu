@@ -121,10 +121,9 @@ struct LvState {
 // Per-warp state in shared memory. Only the first k entries of st[] exist
 // (the layout is cut to the plan's size so that more of the SM's on-chip
 // memory stays L1 cache); never index st[] at or beyond k.
-// Probes each lane keeps in flight in the batched last level.
-#ifndef XM_LEAF_PPL
-#define XM_LEAF_PPL 4
-#endif
+// Probes each lane keeps in flight in the batched last level (measured: 2
+// and 6 are slower; 8 needs more registers than 64).
+constexpr int LEAF_PPL = 4;
 
 // One pair of a batched last level: its driver ids at d[t] for flattened
 // positions t < end (d is offset by the pair's first position), and the list
@@ -139,9 +138,7 @@ struct LeafPair {
 struct WarpSmem {
     int32_t* mtile;  // this warp's MERGE_TILE-id tile for merge intersections
     int32_t m[XM_MAXK];
-#if XM_LEAF_TABLE
     LeafPair lp[32];  // the batched last level's pairs
-#endif
     LvState st[XM_MAXK];
 };
 
@@ -185,29 +182,6 @@ __device__ __forceinline__ int32_t ld(const int32_t* p, int i, bool shared) {
 
 // first index in [lo, hi) with p[idx] >= x
 __device__ __forceinline__ int lbound(const int32_t* p, int lo, int hi, int32_t x, bool shared) {
-#if XM_LB8
-    if (!shared) {
-        // eight-way search in global memory: each round reads seven evenly
-        // spaced ids at once (independent loads) and keeps the eighth of the
-        // range that must hold the answer, so a list of L ids costs about
-        // log8(L) dependent rounds instead of log2(L); the last <= 8 ids are
-        // read together and counted
-        while (hi - lo > 8) {
-            const int r = hi - lo;
-            int c = 0;
-#pragma unroll
-            for (int j = 1; j < 8; j++) c += __ldg(p + lo + (int)(((long long)r * j) >> 3)) < x ? 1 : 0;
-            const int nlo = c ? lo + (int)(((long long)r * c) >> 3) + 1 : lo;
-            const int nhi = c < 7 ? lo + (int)(((long long)r * (c + 1)) >> 3) : hi;
-            lo = nlo;
-            hi = nhi;
-        }
-        int c = 0;
-#pragma unroll
-        for (int j = 0; j < 8; j++) c += (lo + j < hi && __ldg(p + lo + j) < x) ? 1 : 0;
-        return lo + c;
-    }
-#endif
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
         if (ld(p, mid, shared) < x) lo = mid + 1; else hi = mid;
@@ -1116,12 +1090,11 @@ __device__ unsigned long long leaf_batch(const XmPlanDev& P, const GraphDev& g, 
         ptab = F.T ? F.tab : F.p + a0;
         ptn = F.T ? (int)F.T : -na;
     }
-#if XM_LEAF_TABLE
     // Each lane walks the flattened positions lane, lane + 32, ... and keeps
     // the index of the pair its position falls in (pairs only ever advance),
     // reading a pair's pointers from the warp's shared table when it moves
     // on: no shuffles per probe.
-    constexpr int PPL = XM_LEAF_PPL;
+    constexpr int PPL = LEAF_PPL;
     ws.lp[lane] = LeafPair{dptr - pre, ptab, pend, ptn};
     __syncwarp();
     int pi = 0, pe = ws.lp[0].end;
@@ -1164,52 +1137,8 @@ __device__ unsigned long long leaf_batch(const XmPlanDev& P, const GraphDev& g, 
     }
     __syncwarp();
     return cnt;
-#endif
-    for (int t0 = 0; t0 < total; t0 += 128) {
-        int32_t x[4];
-        bool ok[4];
-        const int32_t* tb[4];
-        int tn[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int t = t0 + 32 * u + lane;
-            // pair of position t: the number of pairs whose range ends at or before t
-            int i = 0;
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1)
-                if (__shfl_sync(FULL, pend, i + s - 1) <= t) i += s;
-            const int pi = __shfl_sync(FULL, pre, i);
-            const int32_t* di = shfl_ptr(dptr, i);
-            tb[u] = shfl_ptr(ptab, i);
-            tn[u] = __shfl_sync(FULL, ptn, i);
-            ok[u] = t < total;
-            x[u] = ok[u] ? __ldg(di + (t - pi)) : 0;
-        }
-        bool f[4], dn[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            if (!ok[u]) {
-                f[u] = false;
-                dn[u] = true;
-            } else if (tn[u] > 0) {
-                dn[u] = hash_first(tb[u], (uint32_t)tn[u], x[u], f[u]);
-            } else {
-                const int q = lbound(tb[u], 0, -tn[u], x[u], false);
-                f[u] = q < -tn[u] && __ldg(tb[u] + q) == x[u];
-                dn[u] = true;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            if (ok[u] && !dn[u]) f[u] = hash_has(tb[u], (uint32_t)tn[u], x[u]);
-            for (uint32_t nm = neq; nm && f[u]; nm &= nm - 1) f[u] = x[u] != ws.m[__ffs(nm) - 1];
-            cnt += f[u] ? 1 : 0;
-        }
-    }
-    return cnt;
 }
 
-#if XM_B4
 // The walk below a four-level plan's second level when its last level is a
 // batched two-list level (explore's behaviour for that shape, without the
 // deeper-level and other leaf paths): refill level 2's window from its
@@ -1241,7 +1170,6 @@ __device__ bool walk_last2(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, 
         __syncwarp();
     }
 }
-#endif
 
 // Adds a 128-bit value on lane 0 to the lane's running count, or straight to
 // the 128-bit counter when the 64-bit count would wrap.
@@ -1963,13 +1891,11 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
                 S2.set_shared = 1;
             }
             __syncwarp();
-#if XM_B4
             if (B4) {
                 if (!walk_last2<MODE>(P, g, ws, win, W, batch_leaf_fixed_op(P), lane, ra, acc, st, budget))
                     stop = true;
                 continue;
             }
-#endif
             if (!explore<MODE, PROD, LEAN>(P, g, ws, wins, W, 2, lane, ra, acc, counter, st, budget, 2)) stop = true;
         }
         if (stop) break;
@@ -2326,11 +2252,10 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
     // three-level counts (the last level probed from registers) run the
     // 40-register build, which never merges
     const bool three = mode == MODE_COUNT && !prod && P.k == 3;
-#if XM_B4
+    // four-level plans whose last level is a batched two-list level run a
+    // build without the other level and leaf paths (fewer registers spilled,
+    // less code for the instruction cache)
     const bool b4 = mode == MODE_COUNT && !prod && P.k == 4 && b.l2_units && batch_leaf_fixed_op(P) >= 0;
-#else
-    const bool b4 = false;
-#endif
     const size_t smem = match_smem_bytes(P.k, b.window, warps_per_block, b.merge_ratio > 0 && !three);
     const void* fn = mode == MODE_STATS  ? (prod ? (const void*)k_match<MODE_STATS, true>
                                                  : (const void*)k_match<MODE_STATS, false>)
@@ -2358,10 +2283,8 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
         k_match<MODE_COUNT, true><<<grid, block, smem, stream>>>(plan_dev, b);
     else if (three)
         k_match<MODE_COUNT, false, 3><<<grid, block, smem, stream>>>(plan_dev, b);
-#if XM_B4
     else if (b4)
         k_match<MODE_COUNT, false, XM_MATCH_MINB, true><<<grid, block, smem, stream>>>(plan_dev, b);
-#endif
     else
         k_match<MODE_COUNT, false><<<grid, block, smem, stream>>>(plan_dev, b);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
