@@ -37,6 +37,10 @@ METRIC = "matches/s"
 # kernels one matching pass enqueues: first-level chunks, count, write (each
 # followed by a 3-kernel scan except the write), units + scan, matcher
 LAUNCHES_PER_CALL = 14
+# bytes of one device plan copy (XmPlanDev: 8 levels and 7 product sets of
+# 260 B, plus 52 B of header) and of the control block read back per pass
+PLAN_BYTES = 52 + 15 * 260
+CTL_BYTES = 24 * 8
 
 
 def passes_per_call(plan, subset: bool):
@@ -830,7 +834,8 @@ def main():
         del out
 
     # end to end through the public API with host buffers: pinned arc arrays
-    # -> xm_load_graph (CSR build + upload) -> 13 counts -> readback
+    # -> xm_load_graph (upload, dual CSR and hash index built on the device)
+    # -> the step's counts -> readback
     e2e = None
     if args.e2e_steps > 0:
         hs = torch.from_numpy(src).pin_memory()
@@ -847,12 +852,18 @@ def main():
             ev1.record(stream)
             ev1.synchronize()
             e2e_ms.append(ev0.elapsed_time(ev1))
-            # CSR offsets + lists, hash-index offsets, one plan copy per count
-            h2d = (2 * (g2.n + 1) + 2 * g2.m) * 4 + 2 * (g2.n + 1) * 8 + len(plans) * 1024
             g2.free()
             assert c2 == counts
+        # host -> device: the arc arrays, then per matching pass one plan copy
+        # and (sampled workloads) the staged start-node list; device -> host:
+        # per pass the control block (counts, status), per split its product
+        npass = sum(passes_per_call(p, roots is not None)[0] for p in plans.values())
+        nsplit = sum(passes_per_call(p, roots is not None)[1] for p in plans.values())
+        h2d = hs.numel() * 4 + hd.numel() * 4 + npass * PLAN_BYTES + \
+            (len(plans) * roots.size * 4 if roots is not None else 0)
+        d2h = npass * CTL_BYTES + nsplit * 16
         e2e = {"value": total_matches / (statistics.median(e2e_ms) / 1000.0), "unit": "matches/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(plans) * 128,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": statistics.median(e2e_ms)}
 
     # the whole-graph count of the 5-vertex feed-forward chain through its

@@ -121,9 +121,11 @@ struct LvState {
 // Per-warp state in shared memory. Only the first k entries of st[] exist
 // (the layout is cut to the plan's size so that more of the SM's on-chip
 // memory stays L1 cache); never index st[] at or beyond k.
-// Probes each lane keeps in flight in the batched last level (measured: 2
-// and 6 are slower; 8 needs more registers than 64).
-constexpr int LEAF_PPL = 4;
+// Probes each lane issues per round of the batched last level, with the
+// next round's driver ids already loaded (measured on the scale-24
+// four-level patterns: 2 beats 4 and 6 by 2-13 %; 8 needs more than 64
+// registers).
+constexpr int LEAF_PPL = 2;
 
 // One pair of a batched last level: its driver ids at d[t] for flattened
 // positions t < end (d is offset by the pair's first position), and the list
@@ -986,10 +988,11 @@ __device__ __forceinline__ const T* shfl_ptr(const T* p, int src) {
 // whose longer range is at most ra.merge_ratio times as long are merged, one
 // pair at a time by the whole warp. The other pairs are counted together:
 // the ids of their shorter ranges form one flattened index space that the
-// lanes walk 128 ids per round (four per lane), each id probing the other
-// list of its own pair (its hash table, or a binary search in a list too
-// short for one), so a warp keeps 128 probes in flight however the ids are
-// spread over the pairs. Returns the lane's share of the count.
+// lanes walk LEAF_PPL x 32 ids per round, each id probing the other list of
+// its own pair (its hash table, or a binary search in a list too short for
+// one) while the next round's ids are already being read, so a warp keeps
+// its probes in flight however the ids are spread over the pairs. Returns
+// the lane's share of the count.
 template <int MODE>
 __device__ unsigned long long leaf_batch(const XmPlanDev& P, const GraphDev& g, WarpSmem& ws, int iF,
                                          const int32_t* cand, bool cand_shared, int nb, int lane, const RunArgs& ra,
@@ -1098,18 +1101,36 @@ __device__ unsigned long long leaf_batch(const XmPlanDev& P, const GraphDev& g, 
     ws.lp[lane] = LeafPair{dptr - pre, ptab, pend, ptn};
     __syncwarp();
     int pi = 0, pe = ws.lp[0].end;
+    // software pipeline: the driver ids of the next round are loaded before
+    // this round's buckets, so the two dependent reads of a probe overlap
+    // across rounds
+    int32_t xn[PPL];
+    int qn[PPL];
+#pragma unroll
+    for (int u = 0; u < PPL; u++) {
+        const int t = 32 * u + lane;
+        xn[u] = -1;
+        qn[u] = -1;
+        if (t < total) {
+            while (pe <= t) pe = ws.lp[++pi].end;
+            qn[u] = pi;
+            xn[u] = __ldg(ws.lp[pi].d + t);
+        }
+    }
     for (int t0 = 0; t0 < total; t0 += 32 * PPL) {
         int32_t x[PPL];
         int q[PPL];
 #pragma unroll
         for (int u = 0; u < PPL; u++) {
-            const int t = t0 + 32 * u + lane;
-            x[u] = -1;
-            q[u] = -1;
+            x[u] = xn[u];
+            q[u] = qn[u];
+            const int t = t0 + 32 * PPL + 32 * u + lane;
+            xn[u] = -1;
+            qn[u] = -1;
             if (t < total) {
                 while (pe <= t) pe = ws.lp[++pi].end;
-                q[u] = pi;
-                x[u] = __ldg(ws.lp[pi].d + t);
+                qn[u] = pi;
+                xn[u] = __ldg(ws.lp[pi].d + t);
             }
         }
         bool f[PPL], dn[PPL];
