@@ -409,9 +409,9 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
     const XmLevel& L1 = P.lv[1];
     unsigned long long st_bytes = 0;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    // chunks past the last real one get a zero count
-    if (!WRITE)
-        for (int c = total + wid * 32 + lane; c <= ra.cmax; c += nwarps * 32) ra.chunk_cnt[c] = 0;
+    // the entry after the last real chunk (the scan's terminal) gets a zero
+    // count; the scan reads no further
+    if (!WRITE && wid == 0 && lane == 0) ra.chunk_cnt[total] = 0;
     // warps take runs of consecutive chunks from a counter: a start node's
     // lists are fetched once per run, and the chunks of a hub still spread
     // over many warps
@@ -1449,7 +1449,9 @@ __global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     plan_to_smem(P, plan_g);
     const int E = set_start(ra, ra.n_idx);
     const int ke = ra.pv ? P.prod_p + 1 : P.k;  // levels the count walks
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= ra.emax; e += gridDim.x * blockDim.x) {
+    // the first-level candidates and a terminal zero: the scan reads no further
+    if (blockIdx.x == 0 && threadIdx.x == 0) *reinterpret_cast<int32_t*>(ra.ctl + CTL_ELEN) = E;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= E; e += gridDim.x * blockDim.x) {
         int u = 0;
         if (e < E) {
             const int i = __ldg(ra.l1root + e);
@@ -1746,7 +1748,7 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
     // unit index space: pieces of a start node's first-level set, or pieces
     // of a first-level candidate's second-level driver range
     const int32_t* uprefix = two_level ? ra.units : ra.e_units;
-    const int nidx = two_level ? ra.n_idx : ra.emax;
+    const int nidx = two_level ? ra.n_idx : set_start(ra, ra.n_idx);
     // a work-unit scan that overflowed int32 left wrapped prefixes: walk
     // nothing (the host sees the status bit and retries with larger units)
     if (*((volatile unsigned long long*)(ra.ctl + CTL_STATUS)) & STATUS_OVERFLOW) return;
@@ -2077,7 +2079,9 @@ __device__ __forceinline__ long long block_sum(long long x) {
     return t;  // valid in thread 0
 }
 
-__global__ void k_scan_reduce(const int32_t* __restrict__ v, int64_t len, int64_t* __restrict__ sums) {
+__global__ void k_scan_reduce(const int32_t* __restrict__ v, int64_t len, int64_t* __restrict__ sums,
+                              const int32_t* __restrict__ last) {
+    if (last) len = min(len, (int64_t)__ldg(last) + 1);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     long long s = 0;
     for (int i = threadIdx.x; i < SCAN_TILE; i += blockDim.x)
@@ -2137,8 +2141,11 @@ __global__ void k_scan_top(int64_t* sums, int64_t nb, unsigned long long* __rest
     if (threadIdx.x == 0 && carry > INT_MAX) atomicOr(status, (unsigned long long)STATUS_OVERFLOW);
 }
 
-__global__ void k_scan_down(int32_t* __restrict__ v, int64_t len, const int64_t* __restrict__ sums) {
+__global__ void k_scan_down(int32_t* __restrict__ v, int64_t len, const int64_t* __restrict__ sums,
+                            const int32_t* __restrict__ last) {
+    if (last) len = min(len, (int64_t)__ldg(last) + 1);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    if (base >= len) return;
     const int per = SCAN_TILE / 1024;  // launched with 1024 threads
     long long vals[per];
     for (int j = 0; j < per; j++) {
@@ -2153,12 +2160,15 @@ __global__ void k_scan_down(int32_t* __restrict__ v, int64_t len, const int64_t*
     }
 }
 
-cudaError_t scan_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_t stream) {
+// With `last` (a device int32: the index of the terminal element), only
+// v[0..*last] is scanned; blocks past it return at once. `len` bounds it.
+cudaError_t scan_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_t stream,
+                          const int32_t* last = nullptr) {
     const int64_t nb = (len + SCAN_TILE - 1) / SCAN_TILE;
     if (nb > a.n_block_sums) return cudaErrorInvalidValue;
-    k_scan_reduce<<<(unsigned)nb, 1024, 0, stream>>>(v, len, a.block_sums);
+    k_scan_reduce<<<(unsigned)nb, 1024, 0, stream>>>(v, len, a.block_sums, last);
     k_scan_top<<<1, 1024, 0, stream>>>(a.block_sums, nb, a.ctl + CTL_STATUS);
-    k_scan_down<<<(unsigned)nb, 1024, 0, stream>>>(v, len, a.block_sums);
+    k_scan_down<<<(unsigned)nb, 1024, 0, stream>>>(v, len, a.block_sums, last);
     return cudaGetLastError();
 }
 
@@ -2253,7 +2263,8 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
         k_l1<false, MODE_STATS><<<grid_chunks, 256, 0, stream>>>(plan_dev, b);
     else
         k_l1<false, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, b);
-    if ((err = scan_in_place(b.chunk_cnt, (int64_t)b.cmax + 1, b, stream)) != cudaSuccess) return err;
+    if ((err = scan_in_place(b.chunk_cnt, (int64_t)b.cmax + 1, b, stream, b.root_chunks + b.n_idx)) != cudaSuccess)
+        return err;
     k_l1<true, MODE_COUNT><<<grid_chunks, 256, 0, stream>>>(plan_dev, b);
     // 2. work units: per start node for two-vertex patterns, else per
     // first-level candidate (pieces of the second level's driver range)
@@ -2263,7 +2274,9 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
     } else {
         const int grid_e = (int)std::min<int64_t>(((int64_t)b.emax + 256) / 256, (int64_t)nsm * 16);
         k_l2_units<<<grid_e, 256, 0, stream>>>(plan_dev, b);
-        if ((err = scan_in_place(b.e_units, (int64_t)b.emax + 1, b, stream)) != cudaSuccess) return err;
+        if ((err = scan_in_place(b.e_units, (int64_t)b.emax + 1, b, stream,
+                                 reinterpret_cast<const int32_t*>(b.ctl + CTL_ELEN))) != cudaSuccess)
+            return err;
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // 3. persistent matcher

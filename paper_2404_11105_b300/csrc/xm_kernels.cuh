@@ -83,6 +83,7 @@ enum {
     CTL_W_LAST = 18,   // start, warps
     CTL_W_SUM = 19,
     CTL_W_COUNT = 20,
+    CTL_ELEN = 21,     // low 32 bits: first-level candidates of the pass (e_units' terminal index)
     CTL_WORDS = 24
 };
 
