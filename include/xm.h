@@ -111,12 +111,15 @@ uint64_t xm_device_bytes_live(void);
  *   out        receives the handle.
  *
  * Builds a dual sorted CSR (out-lists and in-lists, each ascending, int32
- * offsets) on the host and copies it to device memory owned by the handle,
- * together with the handle's scratch buffers (about 12 bytes per node and
- * 12 bytes per arc) and a hash index of the lists (up to 16 bytes per arc).
- * The host arrays of the build are kept for the next load (process-wide;
- * about 32 bytes per input arc and 28 bytes per node of the largest graph
- * loaded so far), so loads from several threads take turns.
+ * offsets) on the device, in memory owned by the handle: host arcs are
+ * uploaded, the arcs are packed into 64-bit (src, dst) keys, radix-sorted,
+ * and repeats and self-loops are dropped; the in-lists come from the keys
+ * with their halves swapped and sorted again. Then come the handle's scratch
+ * buffers (about 12 bytes per node and 12 bytes per arc) and a hash index of
+ * the lists of at least 32 ids (up to 16 bytes per arc, built one thread
+ * per list entry). The build's temporaries (about 16 bytes per input arc
+ * for the keys, plus the uploaded arcs) are freed before the call returns.
+ * Synchronises `stream`.
  * Errors: XM_EINVAL for n/m out of range or an id outside [0, n), or more
  * than 2^31-1 arcs after deduplication; XM_ENOMEM; XM_ECUDA.
  */

@@ -1104,33 +1104,57 @@ __device__ unsigned long long leaf_batch(const XmPlanDev& P, const GraphDev& g, 
     // software pipeline: the driver ids of the next round are loaded before
     // this round's buckets, so the two dependent reads of a probe overlap
     // across rounds
+    // the current pair's pointers stay in registers; the shared table is read
+    // only when a lane moves on to the next pair
+    const int32_t* cd = ws.lp[0].d;
+    const int32_t* ctab = ws.lp[0].tab;
+    int cn = ws.lp[0].n;
     int32_t xn[PPL];
-    int qn[PPL];
+    const int32_t* tn[PPL];
+    int nn[PPL];
+    bool okn[PPL];
 #pragma unroll
     for (int u = 0; u < PPL; u++) {
         const int t = 32 * u + lane;
+        okn[u] = t < total;
         xn[u] = -1;
-        qn[u] = -1;
-        if (t < total) {
-            while (pe <= t) pe = ws.lp[++pi].end;
-            qn[u] = pi;
-            xn[u] = __ldg(ws.lp[pi].d + t);
+        tn[u] = nullptr;
+        nn[u] = 0;
+        if (okn[u]) {
+            if (pe <= t) {
+                do { pe = ws.lp[++pi].end; } while (pe <= t);
+                cd = ws.lp[pi].d;
+                ctab = ws.lp[pi].tab;
+                cn = ws.lp[pi].n;
+            }
+            xn[u] = __ldg(cd + t);
+            tn[u] = ctab;
+            nn[u] = cn;
         }
     }
     for (int t0 = 0; t0 < total; t0 += 32 * PPL) {
         int32_t x[PPL];
-        int q[PPL];
+        const int32_t* tb[PPL];
+        int nb_[PPL];
+        bool ok[PPL];
 #pragma unroll
         for (int u = 0; u < PPL; u++) {
             x[u] = xn[u];
-            q[u] = qn[u];
+            tb[u] = tn[u];
+            nb_[u] = nn[u];
+            ok[u] = okn[u];
             const int t = t0 + 32 * PPL + 32 * u + lane;
-            xn[u] = -1;
-            qn[u] = -1;
-            if (t < total) {
-                while (pe <= t) pe = ws.lp[++pi].end;
-                qn[u] = pi;
-                xn[u] = __ldg(ws.lp[pi].d + t);
+            okn[u] = t < total;
+            if (okn[u]) {
+                if (pe <= t) {
+                    do { pe = ws.lp[++pi].end; } while (pe <= t);
+                    cd = ws.lp[pi].d;
+                    ctab = ws.lp[pi].tab;
+                    cn = ws.lp[pi].n;
+                }
+                xn[u] = __ldg(cd + t);
+                tn[u] = ctab;
+                nn[u] = cn;
             }
         }
         bool f[PPL], dn[PPL];
@@ -1138,20 +1162,18 @@ __device__ unsigned long long leaf_batch(const XmPlanDev& P, const GraphDev& g, 
         for (int u = 0; u < PPL; u++) {
             f[u] = false;
             dn[u] = true;
-            if (q[u] >= 0) {
-                const int32_t* tab = ws.lp[q[u]].tab;
-                const int n = ws.lp[q[u]].n;
-                if (n > 0) {
-                    dn[u] = hash_first(tab, (uint32_t)n, x[u], f[u]);
+            if (ok[u]) {
+                if (nb_[u] > 0) {
+                    dn[u] = hash_first(tb[u], (uint32_t)nb_[u], x[u], f[u]);
                 } else {
-                    const int r0 = lbound(tab, 0, -n, x[u], false);
-                    f[u] = r0 < -n && __ldg(tab + r0) == x[u];
+                    const int r0 = lbound(tb[u], 0, -nb_[u], x[u], false);
+                    f[u] = r0 < -nb_[u] && __ldg(tb[u] + r0) == x[u];
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < PPL; u++) {
-            if (!dn[u]) f[u] = hash_has(ws.lp[q[u]].tab, (uint32_t)ws.lp[q[u]].n, x[u]);
+            if (!dn[u]) f[u] = hash_has(tb[u], (uint32_t)nb_[u], x[u]);
             for (uint32_t nm = neq; nm && f[u]; nm &= nm - 1) f[u] = x[u] != ws.m[__ffs(nm) - 1];
             cnt += f[u] ? 1 : 0;
         }
