@@ -2101,18 +2101,23 @@ __device__ __forceinline__ long long block_sum(long long x) {
     return t;  // valid in thread 0
 }
 
+// The scans' tiles: a grid-stride loop over the tiles that hold elements
+// (with `last`: up to the terminal element only), so a capacity-sized array
+// of which little is used costs a few blocks, not one block per tile.
 __global__ void k_scan_reduce(const int32_t* __restrict__ v, int64_t len, int64_t* __restrict__ sums,
                               const int32_t* __restrict__ last) {
     if (last) len = min(len, (int64_t)__ldg(last) + 1);
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    long long s = 0;
-    for (int i = threadIdx.x; i < SCAN_TILE; i += blockDim.x)
-        if (base + i < len) s += v[base + i];
-    s = block_sum(s);
-    if (threadIdx.x == 0) sums[blockIdx.x] = s;
+    const int64_t ntiles = (len + SCAN_TILE - 1) / SCAN_TILE;
+    for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        const int64_t base = b * SCAN_TILE;
+        long long s = 0;
+        for (int i = threadIdx.x; i < SCAN_TILE; i += blockDim.x)
+            if (base + i < len) s += v[base + i];
+        s = block_sum(s);
+        if (threadIdx.x == 0) sums[b] = s;
+        __syncthreads();  // block_sum's shared words are reused by the next tile
+    }
 }
-
-// exclusive scan of one tile held as `per` consecutive values per thread
 template <typename T>
 __device__ void block_exclusive_scan(T* vals, int per, T carry_in, T& total) {
     __shared__ T wtot[32];
@@ -2143,7 +2148,9 @@ __device__ void block_exclusive_scan(T* vals, int per, T carry_in, T& total) {
     __syncthreads();
 }
 
-__global__ void k_scan_top(int64_t* sums, int64_t nb, unsigned long long* __restrict__ status) {
+__global__ void k_scan_top(int64_t* sums, int64_t nb, unsigned long long* __restrict__ status,
+                           const int32_t* __restrict__ last) {
+    if (last) nb = min(nb, ((int64_t)__ldg(last) + SCAN_TILE) / SCAN_TILE);  // tiles holding v[0..*last]
     const int per = 8;
     long long carry = 0;
     for (int64_t base = 0; base < nb; base += (int64_t)blockDim.x * per) {
@@ -2166,31 +2173,37 @@ __global__ void k_scan_top(int64_t* sums, int64_t nb, unsigned long long* __rest
 __global__ void k_scan_down(int32_t* __restrict__ v, int64_t len, const int64_t* __restrict__ sums,
                             const int32_t* __restrict__ last) {
     if (last) len = min(len, (int64_t)__ldg(last) + 1);
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    if (base >= len) return;
+    const int64_t ntiles = (len + SCAN_TILE - 1) / SCAN_TILE;
     const int per = SCAN_TILE / 1024;  // launched with 1024 threads
-    long long vals[per];
-    for (int j = 0; j < per; j++) {
-        int64_t i = base + (int64_t)threadIdx.x * per + j;
-        vals[j] = i < len ? v[i] : 0;
-    }
-    long long tot;
-    block_exclusive_scan<long long>(vals, per, sums[blockIdx.x], tot);
-    for (int j = 0; j < per; j++) {
-        int64_t i = base + (int64_t)threadIdx.x * per + j;
-        if (i < len) v[i] = (int32_t)vals[j];
+    for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        const int64_t base = b * SCAN_TILE;
+        long long vals[per];
+        for (int j = 0; j < per; j++) {
+            int64_t i = base + (int64_t)threadIdx.x * per + j;
+            vals[j] = i < len ? v[i] : 0;
+        }
+        long long tot;
+        block_exclusive_scan<long long>(vals, per, sums[b], tot);
+        for (int j = 0; j < per; j++) {
+            int64_t i = base + (int64_t)threadIdx.x * per + j;
+            if (i < len) v[i] = (int32_t)vals[j];
+        }
+        __syncthreads();  // the scan's shared words are reused by the next tile
     }
 }
-
-// With `last` (a device int32: the index of the terminal element), only
-// v[0..*last] is scanned; blocks past it return at once. `len` bounds it.
 cudaError_t scan_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_t stream,
                           const int32_t* last = nullptr) {
     const int64_t nb = (len + SCAN_TILE - 1) / SCAN_TILE;
     if (nb > a.n_block_sums) return cudaErrorInvalidValue;
-    k_scan_reduce<<<(unsigned)nb, 1024, 0, stream>>>(v, len, a.block_sums, last);
-    k_scan_top<<<1, 1024, 0, stream>>>(a.block_sums, nb, a.ctl + CTL_STATUS);
-    k_scan_down<<<(unsigned)nb, 1024, 0, stream>>>(v, len, a.block_sums, last);
+    int dev = 0, nsm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    // two 1024-thread blocks per SM walk the tiles
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)nsm * 2));
+    k_scan_reduce<<<grid, 1024, 0, stream>>>(v, len, a.block_sums, last);
+    k_scan_top<<<1, 1024, 0, stream>>>(a.block_sums, nb, a.ctl + CTL_STATUS, last);
+    k_scan_down<<<grid, 1024, 0, stream>>>(v, len, a.block_sums, last);
     return cudaGetLastError();
 }
 
