@@ -522,7 +522,9 @@ int xm_graph_last_timing(xm_graph g, float *prep_ms, float *match_ms);
 /*
  * Batched matching: many independent (pattern, graph) matching problems in
  * one persistent kernel launch. Not in the paper, which runs one pattern on
- * one graph; each pair's count is exactly what xm_count returns for it.
+ * one graph; each pair's count is exactly what xm_count returns for it. A
+ * pair walks its plan with the plan's leaf product (Sec. 5.3), never the
+ * cut-vertex decomposition.
  *
  * xm_batch_create -- describe a batch.
  *   np, plans    compiled plans (borrowed handles; they must outlive the

@@ -372,6 +372,7 @@ __device__ __forceinline__ int32_t root_node(const RunArgs& ra, int i) {
     return ra.root_list ? __ldg(ra.root_list + i) : i;
 }
 
+#ifndef XM_BATCH_TU
 // Chunks of the first-level driver list per start node (0 when the node
 // fails the start vertex's degree filter or lies outside [r_lo, r_hi)).
 __global__ void k_l1_chunks(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
@@ -515,6 +516,7 @@ __global__ void k_units(RunArgs ra) {
     }
 }
 
+#endif
 // ------------------------------------------------------ merge intersection
 // Two sorted lists of similar length are intersected by streaming both
 // (Alg. 2's A^{e.dest} cap Pi A^e when no list is much shorter than the
@@ -1465,6 +1467,7 @@ __device__ __forceinline__ int l2_piece(const XmPlanDev& P, const GraphDev& g, i
 // vertices): its second-level driver range cut into pieces (l2_piece), so
 // the work below one hub is spread over many warps. One thread per
 // candidate.
+#ifndef XM_BATCH_TU
 __global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
     __shared__ __align__(16) unsigned char pbuf[plan_bytes(XM_MAXK)];
     XmPlanDev& P = *reinterpret_cast<XmPlanDev*>(pbuf);
@@ -1487,6 +1490,7 @@ __global__ void k_l2_units(const XmPlanDev* __restrict__ plan_g, RunArgs ra) {
         ra.e_units[e] = u;
     }
 }
+#endif
 
 // Three-vertex plans, count mode: the last level of the partial match
 // (m0, m1) over the driver piece [pos0, pos0 + per) of its cut range, with
@@ -1736,6 +1740,7 @@ __device__ unsigned long long leaf_closed_form(const XmPlanDev& P, const GraphDe
 // plans, whose batched last level needs the registers.
 // Resident blocks of 512 threads the matcher's register budget is cut for
 // (2: 64 registers per thread).
+#ifndef XM_BATCH_TU
 #ifndef XM_MATCH_MINB
 #define XM_MATCH_MINB 2
 #endif
@@ -1963,12 +1968,17 @@ __global__ void __launch_bounds__(512, MINB) k_match(const XmPlanDev* __restrict
     }
 }
 
+#endif
+#ifdef XM_BATCH_TU
 // Batched matcher: many (plan, graph) pairs in one persistent launch. A
 // work unit is a block of `root_block` consecutive start nodes of one pair;
 // each warp keeps its own copy of the current pair's plan. The first level
 // is built per start node in a shared-memory window (the graphs are small),
-// then the same Explore() recursion runs; counts go to the pair's counter.
-__global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
+// then the same Explore() recursion runs, ending in the plan's leaf product
+// when it has one; counts go to the pair's counter. Compiled only in the
+// batch translation unit (xm_batch_kernel.cu). 64 registers: at 40 the
+// product walk spilled 896 bytes and the configured batch ran 16 % slower.
+__global__ void __launch_bounds__(512, 2) k_match_batch(BatchDev b) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -2018,6 +2028,9 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
                 for (int i = lane; i < (int)(plan_bytes(__ldg(&b.plans[pg.x].k)) / 4); i += 32)
                     reinterpret_cast<int32_t*>(&P)[i] = reinterpret_cast<const int32_t*>(b.plans + pg.x)[i];
                 g = b.graphs[pg.y];
+                // counts with a leaf product (Sec. 5.3) read its sets from the
+                // device plan in global memory (the shared copy holds levels only)
+                ra.pv = P.prod_r > 0 ? b.plans[pg.x].pv : nullptr;
                 __syncwarp();
             }
             // per-pair budgets count from the start of each unit, so that time a
@@ -2041,8 +2054,12 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
                     continue;
                 }
                 if (!descend<MODE_COUNT>(P, g, ws, wins, W, 1, lane, ra, st)) continue;
-                if (!explore<MODE_COUNT, false>(P, g, ws, wins, W, 1, lane, ra, acc, b.counts + 2 * (size_t)cur, st,
-                                                bud)) {
+                const bool done =
+                    ra.pv ? explore<MODE_COUNT, true>(P, g, ws, wins, W, 1, lane, ra, acc, b.counts + 2 * (size_t)cur,
+                                                      st, bud)
+                          : explore<MODE_COUNT, false>(P, g, ws, wins, W, 1, lane, ra, acc,
+                                                       b.counts + 2 * (size_t)cur, st, bud);
+                if (!done) {
                     stop = !b.pair_budget_ns;  // a pair's budget ends that pair only
                     break;
                 }
@@ -2053,6 +2070,8 @@ __global__ void __launch_bounds__(512, 3) k_match_batch(BatchDev b) {
     if (cur >= 0) flush_count(acc, b.counts + 2 * (size_t)cur, lane);
 }
 
+#endif
+#ifndef XM_BATCH_TU
 // ------------------------------------------------------ cut-vertex split
 // sum over nodes v of prod_{i < t} cnt_i(v), mod 2^128, where cnt_i(v) is
 // the 128-bit counter cnt[i * 2n + 2v .. + 1]; added to out[0..1].
@@ -2207,19 +2226,11 @@ cudaError_t scan_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_
     return cudaGetLastError();
 }
 
+#endif
 }  // namespace
 
+#ifdef XM_BATCH_TU
 size_t batch_warp_bytes(int kmax, int window) { return batch_warp_bytes_impl(kmax, window); }
-
-cudaError_t scan_int32_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_t stream) {
-    return scan_in_place(v, len, a, stream);
-}
-
-size_t match_smem_bytes(int k, int window, int warps, bool merge) {
-    return plan_bytes(k) + match_warp_bytes(k, window, merge) * warps;
-}
-
-int64_t chunk_capacity(int32_t n, int64_t m) { return (int64_t)n + (m + L1_CHUNK - 1) / L1_CHUNK; }
 
 cudaError_t launch_batch(const BatchDev& b, int warps_per_block, int blocks_per_sm, cudaStream_t stream) {
     cudaError_t err;
@@ -2239,6 +2250,17 @@ cudaError_t launch_batch(const BatchDev& b, int warps_per_block, int blocks_per_
     k_match_batch<<<nsm * bps, warps_per_block * 32, smem, stream>>>(b);
     return cudaGetLastError();
 }
+#else
+cudaError_t scan_int32_in_place(int32_t* v, int64_t len, const RunArgs& a, cudaStream_t stream) {
+    return scan_in_place(v, len, a, stream);
+}
+
+size_t match_smem_bytes(int k, int window, int warps, bool merge) {
+    return plan_bytes(k) + match_warp_bytes(k, window, merge) * warps;
+}
+
+int64_t chunk_capacity(int32_t n, int64_t m) { return (int64_t)n + (m + L1_CHUNK - 1) / L1_CHUNK; }
+
 
 cudaError_t launch_root_product(const unsigned long long* cnt, int t, int32_t n, unsigned long long* out,
                                 cudaStream_t stream) {
@@ -2360,5 +2382,7 @@ cudaError_t launch_match(int mode, const XmPlanDev& P, const XmPlanDev* plan_dev
     if (ev && (err = cudaEventRecord(ev[2], stream)) != cudaSuccess) return err;
     return cudaSuccess;
 }
+
+#endif
 
 }  // namespace xm

@@ -19,7 +19,10 @@ def xm():
 @pytest.fixture(scope="module")
 def setup(xm):
     graphs = [synth.small_graph(i, seed=41, n_lo=20, n_hi=300) for i in range(10)]
+    # named patterns, leaf-product patterns (choose and inclusion-exclusion
+    # forms: the batched walk ends in the product), random ones
     pats = [synth.CYCLE3, synth.FFL, synth.BIFAN, synth.CYCLE4, synth.FFCHAIN5, (2, [(0, 1)])] + \
+           [synth.LEAF_PRODUCT_PATTERNS[k] for k in ("out_star4", "path4", "out_star5")] + \
            [synth.batch_pattern(i, seed=43, k_hi=5) for i in range(6)]
     xg = [xm.Graph(*g) for g in graphs]
     og = [oracle.OracleGraph(*g) for g in graphs]
@@ -76,9 +79,10 @@ def test_batch_per_pair_budget(xm, setup):
     pats, xg, og, xp, pairs = setup
     n, src, dst = synth.rmat_graph(14, 16, seed=5)
     heavy_g = xm.Graph(n, src, dst)
-    # an out-star with five leaves walked level by level (the batch has no
-    # leaf products): C(deg, 4)-sized walks below the hubs, seconds at least
-    heavy_p = xm.Plan((6, [(0, 1), (0, 2), (0, 3), (0, 4), (0, 5)]))
+    # a directed 6-cycle: no leaf product and no cut vertex, so the batch
+    # walks all six levels; below the hubs that takes seconds at least
+    heavy_p = xm.Plan((6, [(i, (i + 1) % 6) for i in range(6)]))
+    assert heavy_p.product()["r"] == 0
     graphs = xg + [heavy_g]
     plans = xp + [heavy_p]
     heavy = (len(plans) - 1, len(graphs) - 1)
