@@ -564,7 +564,8 @@ def main():
                     help="device-time budget of each (pattern, graph) pair (0: none)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--ref-budget", type=float, default=8.0)
+    ap.add_argument("--ref-budget", type=float, default=4.0,
+                    help="reference arm: seconds of single-threaded oracle time per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-procs", type=int, default=0,
                     help="also time the oracle in this many concurrent processes (-1: all host cores, at most 64)")
