@@ -67,6 +67,7 @@ struct Budget {
         }
         deadline = __shfl_sync(FULL, t0, 0) + budget_ns;
     }
+#ifdef XM_BATCH_TU
     // A budget of one work unit: the deadline counts from this warp's start
     // of the unit; `st` is shared by all units of the same work (one pair).
     __device__ void start_unit(unsigned long long* st, unsigned long long budget_ns, int lane) {
@@ -76,6 +77,7 @@ struct Budget {
         const unsigned long long now = lane == 0 ? global_ns() : 0ull;
         deadline = __shfl_sync(FULL, now, 0) + budget_ns;
     }
+#endif
     // true when the work must stop (warp-uniform)
     __device__ bool expired(int lane) const {
         if (!deadline) return false;
@@ -154,10 +156,12 @@ __host__ __device__ constexpr size_t warp_state_bytes(int k) {
     return al16(offsetof(WarpSmem, st) + (size_t)k * sizeof(LvState));
 }
 
+#ifdef XM_BATCH_TU
 __host__ __device__ size_t batch_warp_bytes_impl(int kmax, int window) {
     return plan_bytes(kmax) + warp_state_bytes(kmax) + (size_t)(kmax > 2 ? kmax - 2 : 0) * window * sizeof(int32_t) +
            MERGE_TILE * sizeof(int32_t);
 }
+#endif
 
 
 __host__ __device__ constexpr int n_windows(int k) { return k > 3 ? k - 3 : 0; }
@@ -405,7 +409,6 @@ __global__ void __launch_bounds__(256) k_l1(const XmPlanDev* __restrict__ plan_g
     const int ni = ra.n_idx;
     const int lane = threadIdx.x & 31;
     const int total = __ldg(ra.root_chunks + ni);
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const bool filter_deg = P.k > 2;
     const XmLevel& L1 = P.lv[1];
     unsigned long long st_bytes = 0;
