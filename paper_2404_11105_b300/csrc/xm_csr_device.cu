@@ -7,8 +7,8 @@
 // orders the keys by (u, v); equal neighbours are repeats. Self-loops get
 // the key (2^b - 1, 2^b - 1), which sorts after every arc and is dropped
 // with the repeats. The surviving keys give out_adj (their low halves) and
-// out_off (the first position of every row). The in-CSR sorts the same arcs
-// with the halves swapped.
+// out_off (the first position of every row). The in-CSR takes the surviving
+// keys with the halves swapped and sorts them stably by their high half.
 //
 // One radix pass: every warp owns a tile of RADIX_TILE consecutive keys.
 // k_radix_hist counts the tile's digits into hist[digit * tiles + tile]; an
@@ -177,16 +177,16 @@ int grid_for(int64_t items, int nsm) {
 
 }  // namespace
 
-// Sorts keys[0..m) by their low `bits` bits (stable LSD radix sort), using
-// tmp[m] and hist of ceil(m / RADIX_TILE) * RADIX ints; the result ends in
-// *sorted (keys or tmp).
-static cudaError_t radix_sort(unsigned long long* keys, unsigned long long* tmp, int64_t m, int bits, int32_t* hist,
-                              const RunArgs& sa, unsigned long long** sorted, cudaStream_t stream) {
+// Sorts keys[0..m) by their bits [lo_bit, hi_bit) (stable LSD radix sort:
+// keys equal in those bits keep their order), using tmp[m] and hist of
+// ceil(m / RADIX_TILE) * RADIX ints; the result ends in *sorted (keys or tmp).
+static cudaError_t radix_sort(unsigned long long* keys, unsigned long long* tmp, int64_t m, int lo_bit, int hi_bit,
+                              int32_t* hist, const RunArgs& sa, unsigned long long** sorted, cudaStream_t stream) {
     const int ntiles = (int)((m + RADIX_TILE - 1) / RADIX_TILE);
     const int blocks = (ntiles + RADIX_WARPS - 1) / RADIX_WARPS;
     unsigned long long* a = keys;
     unsigned long long* o = tmp;
-    for (int shift = 0; shift < bits; shift += RADIX_BITS) {
+    for (int shift = lo_bit; shift < hi_bit; shift += RADIX_BITS) {
         k_radix_hist<<<blocks, 32 * RADIX_WARPS, 0, stream>>>(a, m, shift, ntiles, hist);
         cudaError_t e = scan_int32_in_place(hist, (int64_t)ntiles * RADIX, sa, stream);
         if (e != cudaSuccess) return e;
@@ -222,7 +222,7 @@ cudaError_t csr_sort_unique(int32_t n, int64_t m, const int32_t* src, const int3
     const unsigned long long loop = ((1ull << b) - 1) << b | ((1ull << b) - 1);
     k_pack_keys<<<grid_for(m, nsm), 256, 0, stream>>>(src, dst, m, b, n, k0, sa.ctl + CTL_STATUS);
     unsigned long long* sorted = nullptr;
-    if ((e = radix_sort(k0, k1, m, 2 * b, ints, sa, &sorted, stream)) != cudaSuccess) return e;
+    if ((e = radix_sort(k0, k1, m, 0, 2 * b, ints, sa, &sorted, stream)) != cudaSuccess) return e;
     unsigned long long* other = sorted == k0 ? k1 : k0;
     k_first_copies<<<grid_for(m, nsm), 256, 0, stream>>>(sorted, m, loop, ints);
     int32_t last[2] = {0, 0};  // the last key's flag, then its scanned position
@@ -254,8 +254,11 @@ cudaError_t csr_emit(int32_t n, unsigned long long* keys, unsigned long long* sp
     k_csr_from_keys<<<grid_for(mm, nsm), 256, 0, stream>>>(keys, mm, b, n, out_off, out_adj);
     k_fill_tail<<<grid_for((int64_t)n + 1, nsm), 256, 0, stream>>>(keys, mm, b, n, out_off);
     k_swap_keys<<<grid_for(mm, nsm), 256, 0, stream>>>(keys, mm, b, spare);
+    // the swapped keys (v, u) come in ascending u within each v (the keys were
+    // sorted by (u, v)), so a stable sort by their high half v completes the
+    // order: half the passes of a full sort
     unsigned long long* sorted = nullptr;
-    if ((e = radix_sort(spare, keys, mm, 2 * b, ints, sa, &sorted, stream)) != cudaSuccess) return e;
+    if ((e = radix_sort(spare, keys, mm, b, 2 * b, ints, sa, &sorted, stream)) != cudaSuccess) return e;
     k_csr_from_keys<<<grid_for(mm, nsm), 256, 0, stream>>>(sorted, mm, b, n, in_off, in_adj);
     k_fill_tail<<<grid_for((int64_t)n + 1, nsm), 256, 0, stream>>>(sorted, mm, b, n, in_off);
     return cudaGetLastError();
