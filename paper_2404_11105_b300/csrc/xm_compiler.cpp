@@ -496,9 +496,12 @@ int decompose(const Pat& P, int flags, Plan& out, std::string& err, bool start_f
         if (rc) return rc;
         if (d->rooted) {
             // the quotient rooted at the cut vertex (label 0): its rooted
-            // matches at node v times |Stab(0)| are its embeddings mapping c to v
+            // matches at node v times |Stab(0)| are its embeddings mapping c to v.
+            // Compiled without reduction: the reduced rooted plans probe
+            // reused first-level sets (no hash table) by binary search
             Plan qr;
-            rc = compile_pattern(qk, (int)s.size(), s.data(), t.data(), sub_flags | XM_NO_SPLIT, qr, err, 0);
+            rc = compile_pattern(qk, (int)s.size(), s.data(), t.data(), sub_flags | XM_NO_SPLIT | XM_NO_REDUCE, qr,
+                                 err, 0);
             if (rc) return rc;
             d->rquots.push_back(std::move(qr));
         }
